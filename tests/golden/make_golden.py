@@ -1,0 +1,62 @@
+"""Writes the stored exact values used by the tests.  Calls only ``oracle/``.
+
+    python tests/golden/make_golden.py [--threads N]
+
+square_L12_exact.txt: exact ln g_kl of the periodic 12x12 square Ising lattice
+(N = 144, N_B = 288) for l = 0..72, every k with g_kl > 0, from the oracle's
+site-by-site transfer matrix (the exact surface that Eq. 2 sums over; the
+paper cites transfer-matrix surfaces up to 12x12).  Columns: l, k, ln g_kl.
+cubic_L3_exact.txt: exact g_kl of the periodic 3x3x3 simple cubic lattice by
+enumeration of all 2^27 configurations.  Columns: l, k, g_kl.
+"""
+import argparse
+import math
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import numpy as np  # noqa: E402
+
+import oracle  # noqa: E402
+
+
+def write_square_l12(threads):
+    t0 = time.time()
+    g = oracle.tm_square(12, ell_max=72, nthreads=threads)
+    path = os.path.join(HERE, "square_L12_exact.txt")
+    with open(path, "w") as f:
+        f.write("# exact ln g_kl, periodic 12x12 square lattice, transfer matrix "
+                "(tests/golden/make_golden.py)\n# l k ln_g\n")
+        for ell in range(73):
+            for k in range(0, 289):
+                if g[k, ell] > 0:
+                    f.write(f"{ell} {k} {math.log(g[k, ell]):.17g}\n")
+    print(f"square L=12: {time.time() - t0:.1f} s -> {path}")
+
+
+def write_cubic_l3():
+    t0 = time.time()
+    g = oracle.brute_force(oracle.CUBIC, 3)
+    path = os.path.join(HERE, "cubic_L3_exact.txt")
+    with open(path, "w") as f:
+        f.write("# exact g_kl, periodic 3x3x3 simple cubic lattice, full enumeration "
+                "(tests/golden/make_golden.py)\n# l k g\n")
+        for ell in range(28):
+            for k in range(82):
+                if g[k, ell] > 0:
+                    f.write(f"{ell} {k} {int(g[k, ell])}\n")
+    print(f"cubic L=3: {time.time() - t0:.1f} s -> {path}")
+
+
+if __name__ == "__main__":
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--threads", type=int, default=os.cpu_count() or 1)
+    ap.add_argument("--only", choices=["square", "cubic"], default=None)
+    a = ap.parse_args()
+    if a.only in (None, "cubic"):
+        write_cubic_l3()
+    if a.only in (None, "square"):
+        write_square_l12(a.threads)

@@ -1,0 +1,268 @@
+"""Pins of the CPU oracle against facts fixed outside the oracle itself.
+
+Every pin here comes from the paper's statements, from closed forms of the
+Ising model, from an independent implementation (numpy enumeration, PyTorch's
+ATen Philox, Python's arbitrary-precision decimal exp), or from exact
+brute-force counts.  No expected value comes from the CUDA library.
+"""
+import math
+import os
+import shutil
+import subprocess
+from decimal import Decimal, getcontext
+
+import numpy as np
+import pytest
+
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10: against PyTorch's host-side at::Philox4_32 (independent code)
+# --------------------------------------------------------------------------
+
+def _aten_helper():
+    exe = os.path.join(HERE, "helpers", "_build", "aten_philox")
+    src = os.path.join(HERE, "helpers", "aten_philox.cpp")
+    if os.path.exists(exe) and os.path.getmtime(exe) >= os.path.getmtime(src):
+        return exe
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    try:
+        from torch.utils.cpp_extension import include_paths
+    except Exception:  # pragma: no cover
+        pytest.skip("torch headers not available")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    cmd = ["g++", "-O1", "-std=c++17"] + ["-I" + p for p in include_paths()] + [src, "-o", exe]
+    subprocess.run(cmd, check=True, capture_output=True)
+    return exe
+
+
+def test_philox_matches_aten_engine():
+    """at::Philox4_32(seed, subseq, offset) runs counter (off_lo, off_hi, sub_lo,
+    sub_hi) with key (seed_lo, seed_hi): the same block the oracle computes."""
+    exe = _aten_helper()
+    rng = np.random.default_rng(12345)
+    cases = [(0, 0, 0), (1, 0, 0), ((7 << 32) | 5, 1, 3), (2**64 - 1, 2**64 - 1, 2**64 - 1)]
+    for _ in range(200):
+        cases.append((int(rng.integers(0, 2**63)) * 2 + int(rng.integers(0, 2)),
+                      int(rng.integers(0, 2**63)), int(rng.integers(0, 2**63))))
+    inp = "".join(f"{s} {q} {o}\n" for s, q, o in cases)
+    out = subprocess.run([exe], input=inp, capture_output=True, text=True, check=True).stdout
+    lines = out.strip().split("\n")
+    assert len(lines) == len(cases)
+    for (seed, sub, off), line in zip(cases, lines):
+        ref = [int(w, 16) for w in line.split()]
+        ctr = [off & 0xFFFFFFFF, off >> 32, sub & 0xFFFFFFFF, sub >> 32]
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        assert list(oracle.philox(ctr, key)) == ref
+
+
+def test_philox_pick_uniformity():
+    """Chi-square of the up/down list picks floor(r n / 2^32) over many steps."""
+    n, draws = 37, 37 * 400
+    counts = np.zeros(n)
+    for t in range(draws):
+        r = oracle.philox([t, 0, 0, 0], [5, 1])
+        counts[(int(r[0]) * n) >> 32] += 1
+    exp = draws / n
+    chi2 = ((counts - exp) ** 2 / exp).sum()
+    assert chi2 < 80.0   # dof 36: P(chi2 > 80) ~ 3e-5
+
+
+# --------------------------------------------------------------------------
+# Exp threshold table: against an exact decimal evaluation
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("u,q_expected", [(1e-6, 13), (1e-7, 16), (1e-8, 20)])
+def test_exp_table_exact(u, q_expected):
+    t, q = oracle.exp_table(u)
+    assert q == q_expected
+    # q is the smallest shift with 4095 * 2^q * u >= 32 ln 2
+    assert 4095 * 2**q * u >= 32 * math.log(2) > 4095 * 2**(q - 1) * u
+    getcontext().prec = 60
+    two32 = Decimal(2) ** 32
+    for i in list(range(0, 4096, 7)) + [4094, 4095]:
+        x = float(i << q) * u                     # the same IEEE double product
+        exact = (Decimal(-x).exp() * two32 + Decimal("0.5"))
+        assert int(t[i]) == int(exact.to_integral_value(rounding="ROUND_FLOOR")), i
+    assert t[0] == 2**32
+    assert np.all(np.diff(t.astype(np.int64)) <= 0)
+    assert t[4095] <= 1
+
+
+@pytest.mark.parametrize("u", [1e-6, 1e-8])
+def test_threshold_interpolation(u):
+    """T(d) tracks 2^32 exp(-u d) within the linear-interpolation bound
+    (2^q u)^2 / 8 (relative) plus rounding, is nonincreasing, and is 0 past
+    the table's end."""
+    t, q = oracle.exp_table(u)
+    h = 2**q * u
+    rng = np.random.default_rng(3)
+    ds = sorted(set([1, 2, 2**q - 1, 2**q, 2**q + 1] +
+                    [int(x) for x in rng.integers(1, 4095 * 2**q, 300)]))
+    prev = 2**32
+    for d in ds:
+        T = oracle.threshold(u, d)
+        ref = 2**32 * math.exp(-u * d)
+        assert T <= prev
+        prev = T
+        assert abs(T - ref) <= ref * (h * h / 8 * 1.01) + 2.0, (d, T, ref)
+        assert T >= ref - 2.0                    # chord of a convex function lies above it
+    assert oracle.threshold(u, 4095 * 2**q) == 0
+    assert oracle.threshold(u, 10**15) == 0
+
+
+# --------------------------------------------------------------------------
+# Exact g_kl: brute force vs an independent numpy enumeration, TM vs brute
+# force, and closed forms (Eq. 2; spectrum ends in the discussion of Fig. 1)
+# --------------------------------------------------------------------------
+
+def _numpy_enumeration(lattice, L):
+    """Enumerate all configurations with numpy; bonds from coordinates."""
+    N = L * L
+    cfg = np.arange(2**N, dtype=np.int64)
+    spins = ((cfg[:, None] >> np.arange(N)[None, :]) & 1).astype(np.int8)
+    grid = spins.reshape(-1, L, L)          # [cfg, y, x]
+    k = (grid != np.roll(grid, 1, axis=2)).sum(axis=(1, 2))
+    k += (grid != np.roll(grid, 1, axis=1)).sum(axis=(1, 2))
+    if lattice == oracle.TRIANGULAR:        # the (x+1, y-1) diagonal
+        k += (grid != np.roll(np.roll(grid, 1, axis=2), -1, axis=1)).sum(axis=(1, 2))
+    ell = spins.sum(axis=1)
+    NB = N * (3 if lattice == oracle.TRIANGULAR else 2)
+    g = np.zeros((NB + 1, N + 1))
+    np.add.at(g, (k, ell), 1)
+    return g
+
+
+@pytest.mark.parametrize("lattice", [oracle.SQUARE, oracle.TRIANGULAR])
+def test_brute_force_matches_numpy(lattice):
+    g = oracle.brute_force(lattice, 4)
+    assert np.array_equal(g, _numpy_enumeration(lattice, 4))
+
+
+@pytest.mark.parametrize("L", [4, 5])
+def test_tm_matches_brute_force(L):
+    assert np.array_equal(oracle.tm_square(L, nthreads=2), oracle.brute_force(oracle.SQUARE, L))
+
+
+def _closed_forms(g, N, NB, z, bipartite):
+    C = [math.comb(N, l) for l in range(N + 1)]
+    ell_max = g.shape[1] - 1
+    for l in range(ell_max + 1):               # micromagnetic degeneracies g_l = C(N, l)
+        assert math.isclose(g[:, l].sum(), C[l], rel_tol=1e-12)
+    assert g[0, 0] == 1 and g[:, 0].sum() == 1  # all down: k = 0
+    assert g[z, 1] == N                         # one up spin: k = z
+    assert g[2 * z - 2, 2] == NB                # two adjacent up spins
+    assert g[2 * z, 2] == C[2] - NB             # two separated up spins
+    if bipartite and ell_max >= N // 2:
+        assert g[NB, N // 2] == 2               # the two Neel states
+
+
+@pytest.mark.parametrize("L", [4, 6, 8])
+def test_tm_square_closed_forms(L):
+    N, NB = L * L, 2 * L * L
+    g = oracle.tm_square(L, nthreads=4)
+    _closed_forms(g, N, NB, 4, True)
+    # periodic square, l = N/2: the minimum k is 2L, from the 2L straight bands
+    col = g[:, N // 2]
+    assert col[:2 * L].sum() == 0 and col[2 * L] == 2 * L
+    for l in range(N + 1):
+        nz = np.nonzero(g[:, l])[0]
+        assert nz.max() == 4 * min(l, N - l)     # scattered minority spins: k = 4 l
+        assert np.all(nz % 2 == 0)               # even degree: k has the parity of z l
+        assert np.allclose(g[:, l], g[:, N - l], rtol=1e-12, atol=0)   # up-down symmetry
+
+
+@pytest.mark.parametrize("lattice,L", [(oracle.TRIANGULAR, 4), (oracle.CUBIC, 3)])
+def test_brute_force_closed_forms(lattice, L):
+    info = oracle.lattice_info(lattice, L)
+    if info["N"] > 16 and os.environ.get("WL_SLOW_TESTS") != "1":
+        L, info = 3, oracle.lattice_info(lattice, 3)
+        if info["N"] > 16:
+            pytest.skip("cubic 3^3 enumeration takes ~10 s; set WL_SLOW_TESTS=1")
+    g = oracle.brute_force(lattice, L)
+    _closed_forms(g, info["N"], info["NB"], info["z"], False)
+    for l in range(info["N"] + 1):
+        assert np.array_equal(g[:, l], g[:, info["N"] - l])
+
+
+# --------------------------------------------------------------------------
+# The walk itself
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("lattice,L", [(oracle.SQUARE, 6), (oracle.TRIANGULAR, 5), (oracle.CUBIC, 3)])
+def test_walk_state_consistent(lattice, L):
+    """After any number of moves the lists, spins and k agree (recount)."""
+    N = oracle.lattice_info(lattice, L)["N"]
+    for ell in [1, 2, N // 3, N // 2]:
+        st = None
+        for budget in [0, 1, 17, 500, 4321]:
+            st = oracle.run_line(lattice, L, ell, 9, 1e-6, 1000, budget=budget, state=st)
+            assert st.t == budget
+            assert oracle.audit(st) == 0
+
+
+def test_walk_bins_and_fixed_point_invariants():
+    st = oracle.run_line(oracle.SQUARE, 6, 18, 4, 1e-6, 1000, budget=200_000)
+    vis = st.visited.astype(bool)
+    # after a stage step the visited minimum of ln g is zero; unvisited stay 0
+    assert np.all(st.lng[~vis] == 0)
+    assert st.hist[vis].sum() == st.t - int(st.sc[oracle.SC_TSTAGE])
+    assert st.F == (10**6) >> (2 * st.stage)
+
+
+@pytest.mark.parametrize("u,stages", [(1e-6, 10), (1e-7, 12), (1e-8, 14)])
+def test_schedule_stage_count(u, stages):
+    """ln f: 1 -> 1/4 -> ... while ln f >= ln f_min; the single-bin line l=1
+    is flat at every check, so it runs exactly this many stages."""
+    st = oracle.run_line(oracle.SQUARE, 4, 1, 1, u, 1000)
+    assert st.converged and st.stage == stages and st.F == 0
+    assert st.t == 1000 * stages
+    assert math.floor(math.log(1 / u, 4)) + 1 == stages
+
+
+def test_walk_visits_exactly_the_reachable_set():
+    """Ergodicity of the exchange move: every k with g_kl > 0 is visited and
+    no other (L=4 square, all lines, converged)."""
+    g = oracle.brute_force(oracle.SQUARE, 4)
+    for ell in range(9):
+        st = oracle.run_line(oracle.SQUARE, 4, ell, 1, 1e-8, 1000)
+        assert st.converged
+        assert set(np.nonzero(st.visited)[0]) == set(np.nonzero(g[:, ell])[0] // 2)
+
+
+def test_assembly_normalisation():
+    """Eq. 4: the assembled line sums to C(N, l); shifts of ln g cancel."""
+    st = oracle.run_line(oracle.SQUARE, 6, 10, 2, 1e-6, 1000, budget=300_000)
+    out = oracle.assemble(36, 10, st.lng, st.visited, 1e-6)
+    vis = st.visited.astype(bool)
+    assert math.isclose(np.exp(out[vis]).sum(), math.comb(36, 10), rel_tol=1e-12)
+    assert np.all(np.isneginf(out[~vis]))
+    out2 = oracle.assemble(36, 10, st.lng + 12345 * vis, st.visited, 1e-6)
+    assert np.allclose(out, out2, atol=1e-9, equal_nan=False) or np.array_equal(out, out2)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_wl_accuracy_square_L4(mode):
+    """Normalised ln g_kl within mean 0.02 / max 0.1 of exact at ln f_min=1e-8
+    over 8 seeds (flatness checked every 10^6 moves: with checks every 1000
+    moves the 80%/80% test passes at the first check of every stage on these
+    <= 17-bin lines and the walk stops far short of that accuracy)."""
+    from concurrent.futures import ThreadPoolExecutor
+    g = oracle.brute_force(oracle.SQUARE, 4)
+
+    def one(args):
+        seed, ell = args
+        st = oracle.run_line(oracle.SQUARE, 4, ell, seed, 1e-8, 10**6, mode=mode)
+        assert st.converged
+        lg = oracle.assemble(16, ell, st.lng, st.visited, 1e-8)
+        ks = np.nonzero(g[:, ell])[0]
+        return np.abs(lg[ks // 2] - np.log(g[ks, ell]))
+
+    with ThreadPoolExecutor(max(1, os.cpu_count() or 1)) as ex:
+        errs = np.concatenate(list(ex.map(one, [(s, l) for s in range(1, 9) for l in range(9)])))
+    assert errs.mean() <= 0.02
+    assert errs.max() <= 0.1
