@@ -1,0 +1,324 @@
+"""Benchmark: Wang-Landau move attempts per second on the micromagnetic lines
+of the 64x64 periodic square Ising lattice (arXiv:1302.2320), one GB300.
+
+A step is one pass of the whole path over one fresh batch: walker
+initialisation for every line l = 0..N/2 (new seed per step), the walk of every
+line for a fixed move budget (spin-exchange proposals, Eq. 3 acceptance, ln g
+and histogram updates, flatness checks every C moves, stage steps ln f -> ln f
+/ 4), and the FP64 assembly of ln g_kl (Eq. 4).  Deterministic mode: the timed
+launch shape is the one whose trajectories the GPU tests compare bit for bit
+with the CPU oracle.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank walks its own
+surface (seed offset by rank): per-GPU work is fixed, scaling is weak, and the
+only cross-rank traffic is the barrier and the max-over-ranks of the timings.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+LATTICE, L = "square", 64
+LN_F_MIN = 1e-6
+FLATNESS = 0.8
+CHECK_INTERVAL = 16384
+MOVES_PER_LINE = 1 << 22
+INT_OPS_PER_MOVE = 124      # algorithmic 32-bit integer operations per move attempt
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _cpu_sample(ells, budget, seed, threads):
+    """Oracle (deterministic mode, as it stands) on a bounded sample of lines."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(ell):
+        st = oracle.run_line(oracle.SQUARE, L, ell, seed, LN_F_MIN, CHECK_INTERVAL,
+                             int(FLATNESS * 1000), budget, 0)
+        return st.t
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        moves = sum(ex.map(one, ells))
+    return moves, time.perf_counter() - t0
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle on this host's cores."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    threads = os.cpu_count() or 1
+    N = L * L
+    ells = list(range(1, N // 2 + 1))          # every walking line of the surface
+    per_step_budget = 1024                      # bounded sample of the workload per step
+    for _ in range(args.warmup):
+        _cpu_sample(ells[:threads], per_step_budget, 1, threads)
+    tot_moves, tot_sec = 0, 0.0
+    for s in range(args.steps):
+        m, sec = _cpu_sample(ells, per_step_budget, 1 + s, threads)
+        tot_moves += m
+        tot_sec += sec
+    value = tot_moves / tot_sec
+    line = {"impl": "reference", "metric": "WL move attempts/sec", "value": value,
+            "unit": "moves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * tot_sec / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"square L={L} periodic, {N // 2 + 1} lines, ln_f_min={LN_F_MIN}, "
+                       f"C={CHECK_INTERVAL}, deterministic; {per_step_budget} moves on each of "
+                       f"lines 1..{N // 2} per step (bounded sample)"},
+            "cpu_baseline": {"value": value, "unit": "moves/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step_budget} moves x {len(ells)} lines per step"},
+            "e2e": {"value": value, "unit": "moves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1302_2320_gb300 as wl
+
+    world, rank, local = _dist()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    torch.cuda.set_device(local)
+    wl.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    N = L * L
+
+    h = wl.Handle(LATTICE, L, deterministic=1, check_interval=CHECK_INTERVAL,
+                  move_budget=args.moves_per_line, slice_moves=args.moves_per_line,
+                  mapping=args.mapping, stream=stream.cuda_stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    def step(seed):
+        h.reset()
+        h.set_option("seed", seed)
+        h.run(LN_F_MIN, FLATNESS)
+        h.assemble()
+
+    seed0 = 1000 * (rank + 1)
+    for w in range(max(args.warmup, 1)):
+        step(seed0 + w)
+    mapping = h.stats()["mapping"]
+    h.set_option("mapping", mapping)            # autotuned choice, fixed for the timed steps
+
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    moves = launches = 0
+    walk_ms = 0.0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        flush.fill_(s)                           # evict the previous step's state from L2
+        ev[s][0].record(stream)
+        step(seed0 + 100 + s)
+        ev[s][1].record(stream)
+        st = h.stats()
+        moves += st["moves"]
+        walk_ms += st["walk_ms"]
+        launches += st["launches"] + 1           # + the assembly kernel
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+
+    # end to end through the C ABI with host buffers: one pass per step including
+    # the device->host copy of the assembled surface into pinned host memory
+    surf_n = h.get_option("bins")
+    host = torch.empty(surf_n, dtype=torch.float64, pin_memory=True).numpy()
+    e2e_moves, e2e_sec = 0, 0.0
+    for s in range(args.steps):
+        flush.fill_(s)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(seed0 + 200 + s)
+        h.get_surface(host)
+        e2e_sec += time.perf_counter() - t0
+        e2e_moves += h.stats()["moves"]
+    clk = clocks.stop() if rank == 0 else None
+
+    vals = torch.tensor([total_ms, e2e_sec, float(moves), float(e2e_moves)], dtype=torch.float64)
+    if dist:
+        mx = vals[:2].clone().to(dev)
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = vals[2:].clone().to(dev)
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        vals = torch.cat([mx.cpu(), sm.cpu()])
+    total_ms, e2e_sec, moves, e2e_moves = [float(x) for x in vals]
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    value = moves / (total_ms / 1000.0)
+    peaks = _peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    props = torch.cuda.get_device_properties(dev)
+    alu_peak = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12       # Tops/s
+    per_rank_moves = moves / world
+    walk_s = walk_ms / 1000.0
+    achieved = per_rank_moves * INT_OPS_PER_MOVE / walk_s / 1e12
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "walk_kernel_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            with open(tfile) as f:
+                tj = json.load(f)
+            if tj.get("moves_per_line") == args.moves_per_line and tj.get("L") == L:
+                traffic = tj.get("dram_bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        ells = [N // 8, N // 4, 3 * N // 8, N // 2]
+        ells = (ells * ((threads + 3) // 4))[:max(threads, 4)]
+        m, sec = _cpu_sample(ells, args.cpu_moves, 1, threads)
+        cpu = {"value": m / sec, "unit": "moves/s", "cores": threads, "kind": "oracle",
+               "sample": f"{args.cpu_moves} moves on each of {len(ells)} walks of lines "
+                         f"N/8, N/4, 3N/8, N/2 (deterministic, C={CHECK_INTERVAL}), {sec:.1f} s"}
+
+    bytes_d2h = surf_n * 8 + 64
+    bytes_h2d = 4 * (N // 2 + 1) + 4096 * 4
+    line = {
+        "metric": "WL move attempts/sec", "value": value, "unit": "moves/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"square L={L} periodic, {N // 2 + 1} lines (l<=N/2), "
+                               f"ln_f_min={LN_F_MIN}, C={CHECK_INTERVAL}, "
+                               f"{args.moves_per_line} moves/line/step, deterministic",
+                   "lattice": LATTICE, "L": L, "lines": N // 2 + 1, "ln_f_min": LN_F_MIN,
+                   "check_interval": CHECK_INTERVAL, "moves_per_line": args.moves_per_line,
+                   "form": "persistent", "mapping": mapping,
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                     "frac": achieved / alu_peak, "traffic": traffic,
+                     "kernel": "walk_kernel", "ops_per_move": INT_OPS_PER_MOVE,
+                     "peak_basis": f"{props.multi_processor_count} SMs x 128 int32 lanes x {sm_max:.0f} MHz"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_moves / e2e_sec, "unit": "moves/s", "h2d_bytes_per_step": bytes_h2d,
+                "d2h_bytes_per_step": bytes_d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "walk_ms_per_step": walk_ms / args.steps,
+    }
+    print(json.dumps(line), flush=True)
+    h.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--moves-per-line", type=int, default=MOVES_PER_LINE)
+    ap.add_argument("--mapping", type=int, default=0)
+    ap.add_argument("--cpu-moves", type=int, default=20_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,168 @@
+/*
+ * wl.h -- C ABI of the GB300 micromagnetic-ensemble Wang-Landau library
+ * (method of B. D. Stosic, "Parallelizing Wang-Landau algorithm in the field:
+ * the micromagnetic ensemble", arXiv:1302.2320).
+ *
+ * The problem (Eq. 1, Eq. 2): for the nearest-neighbour Ising model on a
+ * lattice with N spins and N_B bonds, estimate the degeneracies g_kl, where k
+ * in [0, N_B] counts antiparallel ("unhappy") bonds and l in [0, N] counts up
+ * spins.  The method runs one independent one-dimensional Wang-Landau walk on
+ * k per micromagnetic line l (spin-exchange moves that keep l fixed,
+ * acceptance min(1, g(k|l)/g(k'|l)) of Eq. 3, ln g += ln f and h += 1 at the
+ * current state, an 80%/80% histogram flatness test, ln f -> ln f / 4 until
+ * ln f < ln f_min) and assembles g_kl = C(N,l) * normalised g(k|l) (Eq. 4).
+ * Lines l and N-l are equal by up-down symmetry; only l <= N/2 is walked.
+ *
+ * Conventions for every entry point:
+ *   - Handles are opaque and owned by the library; all device memory and all
+ *     walker state belong to the handle and live across calls.
+ *   - Output buffers are HOST memory owned by the caller.
+ *   - No call aborts the process or traps the GPU.  A CUDA failure returns
+ *     WL_ECUDA; the message is available from wl_last_error() (thread-local).
+ *   - Calls on one handle must not overlap; distinct handles are independent.
+ *   - ln g is held on the device as an int64 count of u = ln f_min (ln f is
+ *     F*u with F an integer, F0 = round(1/u), F >>= 2 per stage; a line
+ *     converges when F reaches 0); the assembled output is FP64.
+ */
+#ifndef WL_H
+#define WL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wl_ctx* wl_handle;
+
+typedef enum {
+    WL_OK = 0,
+    WL_EINVAL = 1,         /* bad argument or option value                       */
+    WL_ENOMEM = 2,         /* allocation failed or exceeds the "hbm_budget" option */
+    WL_ECUDA = 3,          /* a CUDA call failed (message in wl_last_error)      */
+    WL_ETIMEOUT = 4,       /* "timeout_ms" elapsed; state is consistent, resumable */
+    WL_EABORTED = 5,       /* wl_abort() was called; state consistent, resumable */
+    WL_ENOTCONVERGED = 6,  /* "move_budget" reached before every line converged  */
+    WL_EMISMATCH = 7,      /* device exp table differs from the host-built table */
+    WL_ESTATE = 8,         /* call not valid in the handle's current state       */
+    WL_EOVERFLOW = 9       /* a histogram bin would exceed 2^31-1 within a stage */
+} wl_status;
+
+/* Periodic lattices.  Square: site i = y*L + x, neighbours (x+-1, y), (x, y+-1).
+ * Triangular: rhombic LxL torus, the square's neighbours plus (x+1, y-1) and
+ * (x-1, y+1).  Simple cubic: i = (z*L + y)*L + x, +-1 along each axis.
+ * L >= 3 (no double bonds); N <= 2^20. */
+typedef enum { WL_SQUARE = 0, WL_TRIANGULAR = 1, WL_SIMPLE_CUBIC = 2 } wl_lattice;
+
+/* Aggregate counters of a handle (totals over lines l <= N/2). */
+typedef struct {
+    int64_t moves;            /* move attempts made, summed over lines          */
+    int64_t accepts;          /* accepted exchange proposals                    */
+    int64_t checks;           /* flatness checks made                           */
+    int32_t lines;            /* lines walked (l = 0..N/2)                      */
+    int32_t lines_converged;  /* lines with ln f < ln f_min                     */
+    int32_t min_stage;        /* fewest completed stages over lines             */
+    int32_t max_stage;        /* most completed stages over lines               */
+    int32_t mapping;          /* lanes per walker used by the last wl_run       */
+    int32_t form;             /* 0 persistent batched, 1 one launch per line    */
+    int64_t launches;         /* kernels launched by the last wl_run            */
+    double walk_ms;           /* device time of the last wl_run (CUDA events)   */
+    double init_ms;           /* device time of walker initialisation           */
+    double assemble_ms;       /* device time of the last wl_assemble            */
+} wl_stats;
+
+/* Create a handle for an L x L (square, triangular) or L^3 (cubic) periodic
+ * lattice (Eq. 1, "arbitrary lattice").  Computes the line table (bins of
+ * the even k in [0, min(z*min(l, N-l), N_B)], Eq. 2's k range per line);
+ * device memory is allocated at the first wl_run.  *out receives the handle.
+ * Errors: WL_EINVAL (bad lattice or L). */
+wl_status wl_create(wl_lattice lattice, int L, wl_handle* out);
+
+/* Device bytes a handle for (lattice, L) will hold once run, or 0 on bad
+ * arguments.  Used to admit jobs against a memory budget. */
+size_t wl_required_bytes(wl_lattice lattice, int L);
+
+/* Set an integer option before (or between) runs.  Keys:
+ *   "seed"           Philox key word 1 of every walker (default 1)
+ *   "deterministic"  1: integer acceptance against the exp threshold table,
+ *                    bit-identical to the reference walk; 0: FP32 exp (default 1)
+ *   "check_interval" C: flatness is tested whenever t is a multiple of C (default 1000)
+ *   "move_budget"    per-line cap on the move counter t (default 2^62)
+ *   "mapping"        lanes per walker S in {1,2,4,8,16,32}; 0 = autotune (default 0)
+ *   "form"           0: one persistent launch over all lines with a device
+ *                    work queue; 1: one launch per line (default 0)
+ *   "stream"         cudaStream_t (as an integer) for every launch (default: own stream)
+ *   "slice_moves"    moves per line per persistent launch (default 2^20)
+ *   "timeout_ms"     wall-clock limit of one wl_run, 0 = none (default 0)
+ *   "hbm_budget"     refuse to allocate more than this many bytes (default 0 = none)
+ *   "ell_min", "ell_max"  walk only lines in [ell_min, ell_max] (defaults 0, N/2)
+ * Setting "seed", "deterministic" or "check_interval" after a run requires
+ * wl_reset().  Errors: WL_EINVAL (unknown key or bad value), WL_ESTATE. */
+wl_status wl_set_option(wl_handle h, const char* key, int64_t value);
+wl_status wl_get_option(wl_handle h, const char* key, int64_t* value);
+
+/* Run the walks until every selected line has ln f < ln_f_min (returns WL_OK),
+ * the move budget is reached (WL_ENOTCONVERGED), the timeout elapses
+ * (WL_ETIMEOUT) or wl_abort() is called (WL_EABORTED).  ln_f_min in
+ * [1e-10, 0.5]; flatness in (0, 1] is the fraction x of the x/x flatness test
+ * (0.8 = "80% of visited k at or above 80% of the mean"), resolved to 1/1000.
+ * The first run after wl_create or wl_reset initialises every walker (l up
+ * spins at random, up/down index lists, ln g = 0, h = 0, ln f = 1); later runs
+ * continue from the saved state and must pass the same ln_f_min and flatness.
+ * Blocks the calling thread until the run stops. */
+wl_status wl_run(wl_handle h, double ln_f_min, double flatness);
+
+/* Request that a wl_run in progress on another thread stop at its next
+ * flatness check.  Safe to call from any thread. */
+wl_status wl_abort(wl_handle h);
+
+/* Discard walker state (keeps allocations); the next wl_run re-initialises. */
+wl_status wl_reset(wl_handle h);
+
+/* Assemble ln g_kl = ln C(N,l) + ln g(k|l) - ln sum_k' g(k'|l) (Eq. 4 applied
+ * once, FP64) for every walked line on the device.  Unvisited k get -inf. */
+wl_status wl_assemble(wl_handle h);
+
+/* Copy line ell (0..N; ell > N/2 is served by its mirror N-ell) of the last
+ * wl_assemble into out[0..n), n = number of bins, bin b holding k = k_lo +
+ * b*k_step (k_lo = 0, k_step = 2).  If cap < n nothing is copied, *n_out is
+ * set and WL_EINVAL is returned.  Errors: WL_ESTATE before wl_assemble. */
+wl_status wl_get_lng(wl_handle h, int ell, double* out, size_t cap,
+                     int* k_lo, int* k_step, size_t* n_out);
+
+/* Copy every walked line's assembled ln g (l = ell_min..ell_max, ragged, in
+ * order of l) into out; offsets (length lines+1, may be NULL) receives the
+ * start of each line.  *n_out = total bins.  cap too small: WL_EINVAL. */
+wl_status wl_get_surface(wl_handle h, double* out, size_t cap, int64_t* offsets,
+                         size_t offsets_cap, size_t* n_out);
+
+wl_status wl_get_stats(wl_handle h, wl_stats* out);
+
+/* Full state of one line walker, in plain layouts: scal[8] = {k, t, F (ln f
+ * in units of u), stage, accepts, t at stage start, status (0 running,
+ * 1 converged, 2 overflow), flatness checks}; perm[N] = up-spin list in
+ * entries [0, l) followed by the down-spin list; spins[N] = 0/1 per site;
+ * lng, hist, visited: one entry per bin (k = 2b).  Any pointer may be NULL. */
+wl_status wl_get_line_state(wl_handle h, int ell, int64_t* scal, int32_t* perm,
+                            uint8_t* spins, int64_t* lng, int64_t* hist, uint8_t* visited);
+
+/* The device-built exp threshold table of the last run (4096 entries:
+ * round(2^32 exp(-(i 2^q) u)), q the smallest shift with 4095*2^q*u >=
+ * 32 ln 2) and its q.  Errors: WL_ESTATE before the first wl_run. */
+wl_status wl_get_exp_table(wl_handle h, uint64_t* table, int* q);
+
+/* Run the library's device Philox4x32-10 on n counters: out[4i..4i+3] =
+ * Philox(ctr[4i..4i+3], key[2i..2i+1]).  Host arrays.  For verification. */
+wl_status wl_philox(size_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out);
+
+wl_status wl_destroy(wl_handle h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* wl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WL_H */

@@ -1,0 +1,221 @@
+"""GB300-native micromagnetic-ensemble Wang-Landau (arXiv:1302.2320).
+
+Thin ctypes binding over the C ABI in ``include/wl.h``: every function here
+marshals arguments and calls the CUDA library ``_build/libwl.so``; all of the
+walk (initialisation, moves, flatness tests, stage steps, assembly) runs in its
+kernels.  There is no CPU fallback: if the library is missing or fails to load,
+``lib()`` raises.
+
+The C names are kept: ``wl_create``, ``wl_set_option``, ``wl_run``,
+``wl_assemble``, ``wl_get_lng``, ``wl_get_surface``, ``wl_get_stats``,
+``wl_get_line_state``, ``wl_get_exp_table``, ``wl_philox``, ``wl_reset``,
+``wl_abort``, ``wl_destroy``, ``wl_last_error``.  ``Handle`` wraps a handle
+with the same calls as methods.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libwl.so")
+
+WL_SQUARE, WL_TRIANGULAR, WL_SIMPLE_CUBIC = 0, 1, 2
+LATTICES = {"square": WL_SQUARE, "triangular": WL_TRIANGULAR, "cubic": WL_SIMPLE_CUBIC}
+STATUS = {0: "WL_OK", 1: "WL_EINVAL", 2: "WL_ENOMEM", 3: "WL_ECUDA", 4: "WL_ETIMEOUT",
+          5: "WL_EABORTED", 6: "WL_ENOTCONVERGED", 7: "WL_EMISMATCH", 8: "WL_ESTATE",
+          9: "WL_EOVERFLOW"}
+WL_OK, WL_ENOTCONVERGED, WL_ETIMEOUT, WL_EABORTED = 0, 6, 4, 5
+
+EXPORTED = ["wl_create", "wl_required_bytes", "wl_set_option", "wl_get_option", "wl_run",
+            "wl_abort", "wl_reset", "wl_assemble", "wl_get_lng", "wl_get_surface",
+            "wl_get_stats", "wl_get_line_state", "wl_get_exp_table", "wl_philox", "wl_destroy",
+            "wl_last_error"]
+
+
+class WLError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class wl_stats(ctypes.Structure):
+    _fields_ = [("moves", ctypes.c_int64), ("accepts", ctypes.c_int64), ("checks", ctypes.c_int64),
+                ("lines", ctypes.c_int32), ("lines_converged", ctypes.c_int32),
+                ("min_stage", ctypes.c_int32), ("max_stage", ctypes.c_int32),
+                ("mapping", ctypes.c_int32), ("form", ctypes.c_int32),
+                ("launches", ctypes.c_int64), ("walk_ms", ctypes.c_double),
+                ("init_ms", ctypes.c_double), ("assemble_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    from . import buildlib as _b
+    return _b.build(force=force)
+
+
+def lib():
+    """Load libwl.so (raises if it is absent: there is no fallback path)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run __graft_entry__.build() or python -m paper_1302_2320_gb300.buildlib)")
+        L = ctypes.CDLL(LIB_PATH)
+        i32, i64, u32, dbl, sz = ctypes.c_int, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double, ctypes.c_size_t
+        vp, cp = ctypes.c_void_p, ctypes.c_char_p
+        for name in EXPORTED:
+            getattr(L, name).restype = i32
+        L.wl_create.argtypes = [i32, i32, vp]
+        L.wl_required_bytes.argtypes = [i32, i32]
+        L.wl_required_bytes.restype = sz
+        L.wl_set_option.argtypes = [vp, cp, i64]
+        L.wl_get_option.argtypes = [vp, cp, vp]
+        L.wl_run.argtypes = [vp, dbl, dbl]
+        L.wl_abort.argtypes = [vp]
+        L.wl_reset.argtypes = [vp]
+        L.wl_assemble.argtypes = [vp]
+        L.wl_get_lng.argtypes = [vp, i32, vp, sz, vp, vp, vp]
+        L.wl_get_surface.argtypes = [vp, vp, sz, vp, sz, vp]
+        L.wl_get_stats.argtypes = [vp, vp]
+        L.wl_get_line_state.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
+        L.wl_get_exp_table.argtypes = [vp, vp, vp]
+        L.wl_philox.argtypes = [sz, vp, vp, vp]
+        L.wl_destroy.argtypes = [vp]
+        L.wl_last_error.argtypes = []
+        L.wl_last_error.restype = cp
+        _lib = L
+        return L
+
+
+def wl_last_error() -> str:
+    return lib().wl_last_error().decode()
+
+
+def _check(rc: int, where: str, ok=(WL_OK,)) -> int:
+    if rc not in ok:
+        raise WLError(rc, where, wl_last_error())
+    return rc
+
+
+def _p(a: np.ndarray):
+    assert a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def wl_required_bytes(lattice: int, L: int) -> int:
+    return int(lib().wl_required_bytes(lattice, L))
+
+
+def wl_philox(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:
+    """Device Philox4x32-10 blocks: ctr (n, 4) uint32, key (n, 2) uint32."""
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    key = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
+    out = np.zeros_like(ctr)
+    _check(lib().wl_philox(ctr.shape[0], _p(ctr), _p(key), _p(out)), "wl_philox")
+    return out
+
+
+class Handle:
+    """One lattice's set of micromagnetic-line walkers on the GPU."""
+
+    def __init__(self, lattice, L: int, **options):
+        if isinstance(lattice, str):
+            lattice = LATTICES[lattice]
+        self._h = ctypes.c_void_p()
+        _check(lib().wl_create(lattice, L, ctypes.byref(self._h)), "wl_create")
+        self.lattice, self.L = lattice, L
+        self.N = self.get_option("N")
+        self.NB = self.get_option("NB")
+        self.lines = self.get_option("lines")
+        for k, v in options.items():
+            self.set_option(k, v)
+
+    def close(self):
+        if self._h:
+            lib().wl_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_option(self, key: str, value: int):
+        _check(lib().wl_set_option(self._h, key.encode(), int(value)), f"wl_set_option({key})")
+
+    def get_option(self, key: str) -> int:
+        v = ctypes.c_int64()
+        _check(lib().wl_get_option(self._h, key.encode(), ctypes.byref(v)), f"wl_get_option({key})")
+        return v.value
+
+    def run(self, ln_f_min: float, flatness: float = 0.8, allow=(WL_OK, WL_ENOTCONVERGED)) -> int:
+        """wl_run; returns the status (WL_OK or WL_ENOTCONVERGED by default)."""
+        return _check(lib().wl_run(self._h, ln_f_min, flatness), "wl_run", ok=allow)
+
+    def abort(self):
+        _check(lib().wl_abort(self._h), "wl_abort")
+
+    def reset(self):
+        _check(lib().wl_reset(self._h), "wl_reset")
+
+    def assemble(self):
+        _check(lib().wl_assemble(self._h), "wl_assemble")
+
+    def get_lng(self, ell: int) -> np.ndarray:
+        n = ctypes.c_size_t()
+        lib().wl_get_lng(self._h, ell, None, 0, None, None, ctypes.byref(n))
+        out = np.empty(n.value, dtype=np.float64)
+        _check(lib().wl_get_lng(self._h, ell, _p(out), out.size, None, None, None), "wl_get_lng")
+        return out
+
+    def get_surface(self, out: np.ndarray | None = None):
+        """(ln g over all walked lines, ragged offsets)."""
+        n = ctypes.c_size_t()
+        lib().wl_get_surface(self._h, None, 0, None, 0, ctypes.byref(n))
+        if out is None:
+            out = np.empty(n.value, dtype=np.float64)
+        lines = self.get_option("ell_max") - self.get_option("ell_min") + 1
+        offs = np.empty(lines + 1, dtype=np.int64)
+        _check(lib().wl_get_surface(self._h, _p(out), out.size, _p(offs), offs.size, None),
+               "wl_get_surface")
+        return out, offs
+
+    def stats(self) -> dict:
+        s = wl_stats()
+        _check(lib().wl_get_stats(self._h, ctypes.byref(s)), "wl_get_stats")
+        return s.as_dict()
+
+    def line_state(self, ell: int) -> dict:
+        nb = int(min(self.get_option("z") * min(ell, self.N - ell), self.NB) // 2 + 1)
+        d = {"sc": np.zeros(8, dtype=np.int64), "perm": np.zeros(self.N, dtype=np.int32),
+             "spins": np.zeros(self.N, dtype=np.uint8), "lng": np.zeros(nb, dtype=np.int64),
+             "hist": np.zeros(nb, dtype=np.int64), "visited": np.zeros(nb, dtype=np.uint8)}
+        _check(lib().wl_get_line_state(self._h, ell, _p(d["sc"]), _p(d["perm"]), _p(d["spins"]),
+                                       _p(d["lng"]), _p(d["hist"]), _p(d["visited"])),
+               "wl_get_line_state")
+        return d
+
+    def exp_table(self):
+        t = np.zeros(4096, dtype=np.uint64)
+        q = ctypes.c_int()
+        _check(lib().wl_get_exp_table(self._h, _p(t), ctypes.byref(q)), "wl_get_exp_table")
+        return t, q.value

@@ -1,0 +1,208 @@
+// wl_device.cuh -- device building blocks of the micromagnetic-line
+// Wang-Landau walker (arXiv:1302.2320): Philox4x32-10, lattice geometry on
+// bit-packed spins, the change of k under a spin exchange, the fixed-point
+// acceptance of Eq. 3, and warp-group helpers.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace wl {
+
+constexpr uint32_t kVisited = 0x80000000u;   // hist word: bit 31 = bin ever visited
+constexpr int kTableN = 4096;
+constexpr int kTableBytes = kTableN * 4;     // entries 1..4095 as u32; entry 0 is 2^32
+
+enum LatticeType : int { kSquare = 0, kTriangular = 1, kCubic = 2 };
+
+// Per-line scalar state (device, one per walked line).
+struct LineState {
+    int64_t k;         // current number of unhappy bonds
+    int64_t t;         // move attempts made (the Philox step counter)
+    int64_t F;         // ln f in units of u = ln f_min
+    int64_t stage;     // completed flat histograms
+    int64_t accepts;   // accepted proposals
+    int64_t t_stage;   // t at the start of the current stage
+    int64_t status;    // 0 running, 1 converged, 2 histogram overflow, 3 invariant broken
+    int64_t checks;    // flatness checks made
+};
+
+struct LineDesc {
+    int64_t bin_off;   // first bin of this line in the ragged lng/hist arrays
+    int32_t ell;       // number of up spins
+    int32_t nbins;     // bins k = 0, 2, ..., 2*(nbins-1)
+};
+
+struct Geo {
+    int type, L, N, NB, W;   // W = 32-bit words of packed spins per line (multiple of 4)
+    uint64_t magic;          // ceil(2^40 / L): x / L == (x * magic) >> 40 for x < 2^24
+};
+
+// Everything a walker launch needs.  Pointers are device memory.
+struct WalkArgs {
+    Geo g;
+    const LineDesc* desc;
+    LineState* st;
+    void* perm;              // lines x pstride list entries (uint16 if N <= 65536, else uint32)
+    uint32_t* spins;         // lines x W packed spins
+    int64_t* lng;            // ragged ln g / u
+    uint32_t* hist;          // ragged histogram | kVisited
+    const uint32_t* table;   // exp threshold table (kTableN words)
+    const int32_t* order;    // work queue: line indices, most expensive first
+    int32_t* qnext;          // work queue head
+    int32_t nqueue;
+    int32_t q;               // table shift
+    float neg_u_log2e;       // -u * log2(e), production acceptance
+    uint32_t seed;
+    int32_t flat_pm;         // flatness fraction x in 1/1000
+    int32_t stage_smem;      // 1: lists and spins staged in shared memory
+    int32_t slot_bytes;      // shared bytes per walker slot when staged
+    int32_t pstride;         // list entries per line, N rounded up to 16 bytes
+    int64_t C;               // flatness check interval
+    int64_t budget;          // per-line cap on t
+    int64_t slice_moves;     // moves per line in this launch
+    const uint64_t* deadline_ns;      // device globaltimer deadline (0 = none), may be null
+    const volatile int32_t* abort_flag;   // host-mapped stop request, may be null
+    int32_t* flags;          // device flags: bit0 deadline, bit1 aborted, bit2 overflow, bit3 invariant
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products on
+// words 0 and 2 with the state rearranged as (hi1^c1^k0, lo1, hi0^c3^k1, lo0);
+// the key advances by the Weyl increments after every round.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Index in [0, n) from a 32-bit word: floor(r * n / 2^32).
+__device__ __forceinline__ uint32_t pick(uint32_t r, uint32_t n) { return __umulhi(r, n); }
+
+__device__ __forceinline__ uint32_t divL(const Geo& g, uint32_t x)
+{
+    return (uint32_t)(((uint64_t)x * g.magic) >> 40);
+}
+
+__device__ __forceinline__ uint32_t spin_at(const uint32_t* sp, uint32_t n)
+{
+    return (sp[n >> 5] >> (n & 31u)) & 1u;
+}
+
+// Neighbours of site i on the periodic lattice LAT (same rule as wl.h).
+template <int LAT>
+__device__ __forceinline__ void neighbours(const Geo& g, uint32_t i, uint32_t* nb)
+{
+    const uint32_t L = (uint32_t)g.L;
+    if (LAT == kCubic) {
+        const uint32_t r = divL(g, i), x = i - r * L;
+        const uint32_t zc = divL(g, r), y = r - zc * L;
+        const uint32_t xp = x + 1 == L ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;
+        const uint32_t yp = y + 1 == L ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
+        const uint32_t zp = zc + 1 == L ? 0 : zc + 1, zm = zc == 0 ? L - 1 : zc - 1;
+        const uint32_t row = (zc * L + y) * L;
+        nb[0] = row + xp;
+        nb[1] = row + xm;
+        nb[2] = (zc * L + yp) * L + x;
+        nb[3] = (zc * L + ym) * L + x;
+        nb[4] = (zp * L + y) * L + x;
+        nb[5] = (zm * L + y) * L + x;
+    } else {
+        const uint32_t y = divL(g, i), x = i - y * L;
+        const uint32_t xp = x + 1 == L ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;
+        const uint32_t yp = y + 1 == L ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
+        nb[0] = y * L + xp;
+        nb[1] = y * L + xm;
+        nb[2] = yp * L + x;
+        nb[3] = ym * L + x;
+        if (LAT == kTriangular) {
+            nb[4] = ym * L + xp;
+            nb[5] = yp * L + xm;
+        }
+    }
+}
+
+template <int LAT> struct Coord { static constexpr int z = LAT == kSquare ? 4 : 6; };
+
+// Change of k when up-spin i and down-spin j are exchanged.  With u_i, u_j the
+// up neighbours of i and j in the current configuration and a_ij the number
+// of bonds between them, each bond (i, m), m != j, turns from unhappy to happy
+// or back according to s_m, giving 2u_i - z; the bonds of j give -(2u_j - z);
+// the i-j bond stays unhappy but was counted -1 on each side, so
+//     dk = 2 (u_i - u_j + a_ij).
+template <int LAT>
+__device__ __forceinline__ int delta_k(const Geo& g, const uint32_t* sp, uint32_t i, uint32_t j)
+{
+    constexpr int z = Coord<LAT>::z;
+    uint32_t ni[z], nj[z];
+    neighbours<LAT>(g, i, ni);
+    neighbours<LAT>(g, j, nj);
+    int ui = 0, uj = 0, a = 0;
+#pragma unroll
+    for (int m = 0; m < z; ++m) {
+        ui += (int)spin_at(sp, ni[m]);
+        uj += (int)spin_at(sp, nj[m]);
+        a += (int)(ni[m] == j);
+    }
+    return 2 * (ui - uj + a);
+}
+
+// Eq. 3 for an uphill move of d > 0 units of u.
+//  deterministic: accept iff r < T(d), T linearly interpolated in the table
+//  production:    accept iff U24(r) < 2^(-d u log2 e) in FP32
+template <bool DET>
+__device__ __forceinline__ bool accept_uphill(int64_t d, uint32_t r, const uint32_t* tab, int q,
+                                              float neg_u_log2e)
+{
+    if (DET) {
+        const uint64_t i = (uint64_t)d >> q;
+        if (i >= (uint64_t)(kTableN - 1)) return false;
+        const uint64_t t0 = i == 0 ? (1ull << 32) : (uint64_t)tab[i];
+        const uint64_t t1 = (uint64_t)tab[i + 1];
+        const uint64_t fr = (uint64_t)d & ((1ull << q) - 1ull);
+        const uint64_t T = t0 - (((t0 - t1) * fr) >> q);
+        return (uint64_t)r < T;
+    } else {
+        const float p = exp2f((float)d * neg_u_log2e);
+        return (float)(r >> 8) * 0x1p-24f < p;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Group helpers: S consecutive lanes of a warp serve one walker.
+// ---------------------------------------------------------------------------
+template <int S, typename T>
+__device__ __forceinline__ T group_sum(unsigned gmask, T v)
+{
+#pragma unroll
+    for (int off = S / 2; off > 0; off >>= 1) v += __shfl_xor_sync(gmask, v, off);
+    return v;
+}
+
+template <int S>
+__device__ __forceinline__ int64_t group_min(unsigned gmask, int64_t v)
+{
+#pragma unroll
+    for (int off = S / 2; off > 0; off >>= 1) {
+        const int64_t o = __shfl_xor_sync(gmask, v, off);
+        v = o < v ? o : v;
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+}  // namespace wl

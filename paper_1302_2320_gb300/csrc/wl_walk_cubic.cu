@@ -1,0 +1,12 @@
+// wl_walk_cubic.cu -- walker instantiations for the periodic cubic lattice.
+#include "wl_walk_inst.cuh"
+
+namespace wl {
+
+cudaError_t launch_walk_cubic(int S, bool det, bool idx16, dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, const WalkArgs& a, int* bps)
+{
+    return walk_dispatch<kCubic>(S, det, idx16, grid, block, smem, s, a, bps);
+}
+
+}  // namespace wl

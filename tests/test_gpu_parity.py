@@ -1,0 +1,239 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Deterministic mode must match the oracle bit for bit: list order, spins, k, t,
+ln g (int64 fixed point), histograms, visited sets, ln f and stage counters,
+for every walker-to-lane mapping and both launch forms.  Assembly (FP64) must
+match within 1e-10.  Production mode is checked against exact g_kl.
+"""
+import math
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1302_2320_gb300 as wl
+
+pytestmark = pytest.mark.gpu
+
+THREADS = max(1, min(os.cpu_count() or 1, 32))
+LAT = {"square": oracle.SQUARE, "triangular": oracle.TRIANGULAR, "cubic": oracle.CUBIC}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    wl.build()
+    oracle.build()
+
+
+def oracle_lines(lattice, L, ells, seed, u, C, budget, mode=0):
+    def one(ell):
+        return oracle.run_line(lattice, L, ell, seed, u, C, 800, budget, mode)
+    with ThreadPoolExecutor(THREADS) as ex:
+        return dict(zip(ells, ex.map(one, ells)))
+
+
+def assert_line_equal(h, ell, ref, what=""):
+    g = h.line_state(ell)
+    tag = f"{what} ell={ell}"
+    assert np.array_equal(g["sc"], ref.sc), (tag, g["sc"], ref.sc)
+    assert np.array_equal(g["perm"], ref.perm), tag
+    assert np.array_equal(g["spins"], ref.spins), tag
+    assert np.array_equal(g["lng"], ref.lng), tag
+    assert np.array_equal(g["hist"], ref.hist), tag
+    assert np.array_equal(g["visited"], ref.visited), tag
+
+
+def run_gpu(lattice, L, seed, u, C, budget, mapping=0, form=0, det=1, ell_range=None, **opt):
+    h = wl.Handle(lattice, L, seed=seed, check_interval=C, move_budget=budget, mapping=mapping,
+                  form=form, deterministic=det, **opt)
+    if ell_range:
+        h.set_option("ell_min", ell_range[0])
+        h.set_option("ell_max", ell_range[1])
+    h.run(u, 0.8)
+    return h
+
+
+# --------------------------------------------------------------------------
+# building blocks
+# --------------------------------------------------------------------------
+
+def test_philox_device_matches_oracle():
+    rng = np.random.default_rng(7)
+    n = 4096
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2**32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    key[0] = 0
+    out = wl.wl_philox(ctr, key)
+    for i in range(0, n, 7):
+        assert list(out[i]) == list(oracle.philox(ctr[i], key[i]))
+
+
+@pytest.mark.parametrize("u", [1e-6, 1e-7, 1e-8])
+def test_exp_table_bit_equal(u):
+    h = run_gpu("square", 4, 1, u, 1000, 0)
+    t, q = h.exp_table()
+    ot, oq = oracle.exp_table(u)
+    assert q == oq
+    assert np.array_equal(t, ot)
+
+
+@pytest.mark.parametrize("lattice,L", [("square", 4), ("square", 5), ("square", 12),
+                                       ("triangular", 6), ("cubic", 4), ("square", 64)])
+def test_initial_state_matches_oracle(lattice, L):
+    h = run_gpu(lattice, L, 3, 1e-6, 1000, 0)
+    N = h.N
+    ells = sorted(set([0, 1, 2, N // 4, N // 2 - 1, N // 2]))
+    ref = oracle_lines(LAT[lattice], L, ells, 3, 1e-6, 1000, 0)
+    for ell in ells:
+        assert_line_equal(h, ell, ref[ell], "init")
+
+
+# --------------------------------------------------------------------------
+# deterministic trajectories
+# --------------------------------------------------------------------------
+
+def test_square_L4_converged_bit_exact():
+    """Config 1: L=4, all 9 lines to ln f_min = 1e-8 with checks every 1000 moves."""
+    ref = oracle_lines(oracle.SQUARE, 4, range(9), 1, 1e-8, 1000, 2**62)
+    for mapping in [1, 4, 32]:
+        h = run_gpu("square", 4, 1, 1e-8, 1000, 2**62, mapping=mapping)
+        st = h.stats()
+        assert st["lines_converged"] == 9
+        for ell in range(9):
+            assert_line_equal(h, ell, ref[ell], f"S={mapping}")
+        h.assemble()
+        for ell in range(17):
+            r = ref[min(ell, 16 - ell)]
+            exp = oracle.assemble(16, ell, r.lng, r.visited, 1e-8)
+            got = h.get_lng(ell)
+            fin = np.isfinite(exp)
+            assert np.array_equal(fin, np.isfinite(got))
+            assert np.allclose(got[fin], exp[fin], rtol=0, atol=1e-10)
+
+
+@pytest.fixture(scope="module")
+def l12_ref():
+    """Config 2 deterministic: L=12, 73 lines, 10^7 moves per line (seed 1)."""
+    return oracle_lines(oracle.SQUARE, 12, range(73), 1, 1e-8, 1000, 10**7)
+
+
+@pytest.mark.parametrize("mapping,form", [(1, 0), (2, 0), (4, 0), (8, 0), (16, 0), (32, 0),
+                                          (8, 1), (1, 1)])
+def test_square_L12_bit_exact(l12_ref, mapping, form):
+    h = run_gpu("square", 12, 1, 1e-8, 1000, 10**7, mapping=mapping, form=form,
+                slice_moves=3_000_001)
+    for ell in range(73):
+        assert_line_equal(h, ell, l12_ref[ell], f"S={mapping} form={form}")
+
+
+@pytest.mark.parametrize("lattice,L,budget", [("triangular", 6, 400_000), ("cubic", 4, 300_000),
+                                              ("square", 5, 500_000), ("square", 3, 200_000)])
+def test_other_lattices_bit_exact(lattice, L, budget):
+    h = run_gpu(lattice, L, 5, 1e-6, 777, budget, mapping=8)
+    N = h.N
+    ref = oracle_lines(LAT[lattice], L, range(N // 2 + 1), 5, 1e-6, 777, budget)
+    for ell in range(N // 2 + 1):
+        assert_line_equal(h, ell, ref[ell], lattice)
+
+
+def test_square_L64_sampled_lines_bench_launch():
+    """The L=64 workload in the benchmark's launch shape (autotuned mapping,
+    persistent form, slices): sampled lines against the oracle."""
+    budget = 1 << 20
+    h = run_gpu("square", 64, 1, 1e-6, 16384, budget, slice_moves=1 << 18)
+    ells = [1, 2, 3, 511, 1024, 1500, 2047, 2048]
+    ref = oracle_lines(oracle.SQUARE, 64, ells, 1, 1e-6, 16384, budget)
+    for ell in ells:
+        assert_line_equal(h, ell, ref[ell], "L64")
+    st = h.stats()
+    assert st["moves"] == 2048 * budget          # l = 0 has no move
+    h.assemble()
+    for ell in [2048, 4095 - 2047, 3]:
+        r = ref[min(ell, 4096 - ell)]
+        exp = oracle.assemble(4096, ell, r.lng, r.visited, 1e-6)
+        got = h.get_lng(ell)
+        fin = np.isfinite(exp)
+        assert np.array_equal(fin, np.isfinite(got))
+        assert np.allclose(got[fin], exp[fin], rtol=0, atol=1e-9)
+
+
+def test_continued_runs_equal_single_run():
+    """Slices, repeated wl_run calls and resumption after a budget stop leave
+    the trajectory unchanged (counter-based random numbers)."""
+    a = run_gpu("square", 8, 2, 1e-7, 500, 600_000, mapping=4)
+    b = wl.Handle("square", 8, seed=2, check_interval=500, mapping=32, slice_moves=12345)
+    for budget in [1, 99_999, 250_000, 600_000]:
+        b.set_option("move_budget", budget)
+        b.run(1e-7, 0.8)
+    for ell in range(33):
+        ga, gb = a.line_state(ell), b.line_state(ell)
+        for k in ga:
+            assert np.array_equal(ga[k], gb[k]), (ell, k)
+
+
+def test_line_subset_and_reset():
+    h = run_gpu("square", 6, 4, 1e-6, 1000, 50_000, ell_range=(5, 12))
+    ref = oracle_lines(oracle.SQUARE, 6, [5, 12], 4, 1e-6, 1000, 50_000)
+    assert_line_equal(h, 5, ref[5])
+    assert_line_equal(h, 12, ref[12])
+    assert h.stats()["moves"] == 8 * 50_000
+    h.reset()
+    h.set_option("seed", 9)
+    h.run(1e-6, 0.8)
+    ref9 = oracle_lines(oracle.SQUARE, 6, [7], 9, 1e-6, 1000, 50_000)
+    assert_line_equal(h, 7, ref9[7])
+
+
+def test_symmetric_lines_and_surface():
+    h = run_gpu("square", 6, 1, 1e-6, 1000, 2**62)
+    assert h.stats()["lines_converged"] == 19
+    h.assemble()
+    for ell in range(37):
+        a, b = h.get_lng(ell), h.get_lng(36 - ell)
+        assert np.array_equal(a, b)
+        fin = np.isfinite(a)
+        assert math.isclose(np.exp(a[fin]).sum(), math.comb(36, ell), rel_tol=1e-9)
+    surf, offs = h.get_surface()
+    assert offs[-1] == surf.size
+    assert np.array_equal(surf[offs[10]:offs[11]], h.get_lng(10))
+
+
+def test_errors_are_reported_not_raised_on_device():
+    h = wl.Handle("square", 4)
+    with pytest.raises(wl.WLError):
+        h.run(0.0, 0.8)
+    with pytest.raises(wl.WLError):
+        h.run(1e-6, 1.5)
+    with pytest.raises(wl.WLError):
+        h.set_option("mapping", 3)
+    with pytest.raises(wl.WLError):
+        h.get_lng(3)                       # before assembly
+    h.set_option("move_budget", 10)
+    assert h.run(1e-6) == wl.WL_ENOTCONVERGED
+    with pytest.raises(wl.WLError):
+        h.set_option("seed", 2)            # walk already started
+    with pytest.raises(wl.WLError):
+        h.run(1e-7)                        # a continued run keeps ln f_min
+
+
+# --------------------------------------------------------------------------
+# production mode against exact values
+# --------------------------------------------------------------------------
+
+def test_production_accuracy_square_L4():
+    g = oracle.brute_force(oracle.SQUARE, 4)
+    errs = []
+    for seed in range(1, 9):
+        h = run_gpu("square", 4, seed, 1e-8, 10**6, 2**62, det=0)
+        assert h.stats()["lines_converged"] == 9
+        h.assemble()
+        for ell in range(17):
+            ks = np.nonzero(g[:, ell])[0]
+            got = h.get_lng(ell)
+            assert set(np.nonzero(np.isfinite(got))[0]) == set(ks // 2)
+            errs.append(np.abs(got[ks // 2] - np.log(g[ks, ell])))
+    errs = np.concatenate(errs)
+    assert errs.mean() <= 0.02 and errs.max() <= 0.1, (errs.mean(), errs.max())

@@ -266,3 +266,46 @@ def test_wl_accuracy_square_L4(mode):
         errs = np.concatenate(list(ex.map(one, [(s, l) for s in range(1, 9) for l in range(9)])))
     assert errs.mean() <= 0.02
     assert errs.max() <= 0.1
+
+
+# --------------------------------------------------------------------------
+# The stored exact L=12 surface (tests/golden/square_L12_exact.txt, written by
+# tests/golden/make_golden.py from the oracle's transfer matrix)
+# --------------------------------------------------------------------------
+
+def load_l12_exact():
+    path = os.path.join(HERE, "golden", "square_L12_exact.txt")
+    data = np.loadtxt(path, comments="#")
+    out = {}
+    for ell, k, lg in data:
+        out.setdefault(int(ell), {})[int(k)] = float(lg)
+    return out
+
+
+def test_golden_l12_closed_forms():
+    g = load_l12_exact()
+    L, N, NB = 12, 144, 288
+    assert sorted(g) == list(range(73))
+    for ell, row in g.items():
+        # g_l = C(N, l) (sum over k), in log space
+        lse = np.logaddexp.reduce(np.array(list(row.values())))
+        assert math.isclose(lse, math.log(math.comb(N, ell)), rel_tol=0, abs_tol=1e-11), ell
+        assert max(row) == 4 * ell and all(k % 2 == 0 for k in row)
+    assert g[0] == {0: 0.0}
+    assert math.isclose(g[1][4], math.log(N), abs_tol=1e-12)
+    assert math.isclose(g[2][6], math.log(NB), abs_tol=1e-12)
+    assert math.isclose(g[2][8], math.log(math.comb(N, 2) - NB), abs_tol=1e-12)
+    assert min(g[72]) == 2 * L and math.isclose(g[72][2 * L], math.log(2 * L), abs_tol=1e-12)
+    assert math.isclose(g[72][NB], math.log(2), abs_tol=1e-12)
+
+
+def test_golden_l12_matches_tm_rows_at_small_l():
+    """Low-l rows of the stored surface recomputed with a TM truncated at l=3."""
+    g = load_l12_exact()
+    tm = oracle.tm_square(12, ell_max=3, nthreads=os.cpu_count() or 1) if os.environ.get(
+        "WL_SLOW_TESTS") == "1" else None
+    if tm is None:
+        pytest.skip("set WL_SLOW_TESTS=1 (12x12 TM with l <= 3 takes ~1 min)")
+    for ell in range(4):
+        for k, lg in g[ell].items():
+            assert math.isclose(lg, math.log(tm[k, ell]), abs_tol=1e-12)
