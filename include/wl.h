@@ -60,6 +60,7 @@ typedef struct {
     int64_t moves;            /* move attempts made, summed over lines          */
     int64_t accepts;          /* accepted exchange proposals                    */
     int64_t checks;           /* flatness checks made                           */
+    int64_t batches;          /* speculative batches evaluated (moves per batch = moves / batches) */
     int32_t lines;            /* lines walked (l = 0..N/2)                      */
     int32_t lines_converged;  /* lines with ln f < ln f_min                     */
     int32_t min_stage;        /* fewest completed stages over lines             */

@@ -44,6 +44,7 @@ class WLError(RuntimeError):
 
 class wl_stats(ctypes.Structure):
     _fields_ = [("moves", ctypes.c_int64), ("accepts", ctypes.c_int64), ("checks", ctypes.c_int64),
+                ("batches", ctypes.c_int64),
                 ("lines", ctypes.c_int32), ("lines_converged", ctypes.c_int32),
                 ("min_stage", ctypes.c_int32), ("max_stage", ctypes.c_int32),
                 ("mapping", ctypes.c_int32), ("form", ctypes.c_int32),

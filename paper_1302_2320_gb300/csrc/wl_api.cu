@@ -215,6 +215,8 @@ struct wl_ctx {
     // captured slice graph
     cudaGraphExec_t graph = nullptr;
     int graph_S = -1, graph_stage = -1;
+    unsigned graph_grid = 0, graph_block = 0;
+    WalkArgs graph_args{};          // arguments baked into the captured graph
 };
 
 namespace {
@@ -304,6 +306,9 @@ Geo make_geo(const wl_ctx* h)
     g.NB = h->g.NB;
     g.W = h->lo.W;
     g.magic = (((uint64_t)1 << 40) + (uint64_t)h->g.L - 1) / (uint64_t)h->g.L;
+    g.lshift = 0;
+    while ((1 << (g.lshift + 1)) <= h->g.L) ++g.lshift;
+    g.lmask = (uint32_t)h->g.L - 1u;
     return g;
 }
 
@@ -414,6 +419,8 @@ WalkArgs base_args(wl_ctx* h)
     return a;
 }
 
+int kernel_lattice(const wl_ctx* h);
+
 // Launch shape of the persistent form for S lanes per walker: stage lists and
 // spins in shared memory when at least one warp of walkers fits.
 struct Shape {
@@ -426,29 +433,55 @@ struct Shape {
 wl_status persistent_shape(wl_ctx* h, int S, int* blocks_per_sm_out, Shape* sh)
 {
     const size_t isz = h->lo.idx16 ? 2 : 4;
-    const size_t slot = (size_t)h->lo.pstride * isz + (size_t)h->lo.W * 4;
-    const size_t budget = std::min<size_t>(h->max_smem, 200 * 1024);
+    const size_t stg = (size_t)h->lo.pstride * isz + (size_t)h->lo.W * 4;
+    const size_t cap = std::min<size_t>(h->max_smem, 220 * 1024) - kTableBytes;
     const int groups_per_warp = 32 / S;
-    int threads = 256;
-    int stage = 0;
-    const size_t warps_fit = (budget - kTableBytes) / (slot * groups_per_warp);
-    if (warps_fit >= 1 && slot <= 64 * 1024) {
+    int stage = 0, max_warps = 0;
+    size_t slot = kWinBytes;
+    const size_t warps_staged = cap / ((size_t)groups_per_warp * (kWinBytes + stg));
+    if (warps_staged >= 1 && stg <= 64 * 1024) {
         stage = 1;
-        threads = (int)std::min<size_t>(8, warps_fit) * 32;
+        slot = kWinBytes + stg;
+        max_warps = (int)std::min<size_t>(8, warps_staged);
+    } else {
+        max_warps = (int)std::min<size_t>(8, cap / ((size_t)groups_per_warp * kWinBytes));
     }
-    const size_t smem = kTableBytes + (stage ? (size_t)(threads / S) * slot : 0);
-    int bps = 0;
-    CU(walk_kernel_attrs(h->g.type, S, h->det != 0, h->lo.idx16, smem, threads, &bps));
-    if (bps < 1) return fail(WL_ECUDA, "walker kernel cannot be resident (S=%d smem=%zu)", S, smem);
+    if (max_warps < 1) return fail(WL_ECUDA, "no walker shape fits shared memory (S=%d)", S);
+    // The smallest block that still holds every queued line in one wave spreads
+    // the walkers over the most SMs; otherwise take the largest capacity.
+    int best_w = 0, best_bps = 0;
+    long best_cap = -1;
+    for (int w = 1; w <= max_warps; ++w) {
+        const int threads = w * 32;
+        const size_t smem = kTableBytes + (size_t)(threads / S) * slot;
+        int bps = 0;
+        CU(walk_kernel_attrs(kernel_lattice(h), S, h->det != 0, h->lo.idx16, smem, threads, &bps));
+        if (bps < 1) continue;
+        const long capy = (long)h->num_sms * bps * (threads / S);
+        if (capy >= h->nqueue) {
+            best_w = w;
+            best_bps = bps;
+            best_cap = capy;
+            break;
+        }
+        if (capy > best_cap) {
+            best_w = w;
+            best_bps = bps;
+            best_cap = capy;
+        }
+    }
+    if (best_w == 0) return fail(WL_ECUDA, "walker kernel cannot be resident (S=%d)", S);
+    const int threads = best_w * 32;
+    const size_t smem = kTableBytes + (size_t)(threads / S) * slot;
     const int groups_per_block = threads / S;
     const int need_blocks = (h->nqueue + groups_per_block - 1) / groups_per_block;
-    const int blocks = std::max(1, std::min(need_blocks, h->num_sms * bps));
+    const int blocks = std::max(1, std::min(need_blocks, h->num_sms * best_bps));
     sh->grid = dim3(blocks);
     sh->block = dim3(threads);
     sh->smem = smem;
     sh->stage = stage;
     sh->slot = (int)slot;
-    if (blocks_per_sm_out) *blocks_per_sm_out = bps;
+    if (blocks_per_sm_out) *blocks_per_sm_out = best_bps;
     return WL_OK;
 }
 
@@ -459,7 +492,7 @@ wl_status enqueue_slice(wl_ctx* h, int S, const Shape& sh)
     a.stage_smem = sh.stage;
     a.slot_bytes = sh.slot;
     CU(cudaMemsetAsync(a.qnext, 0, 4, h->s));
-    CU(launch_walk(h->g.type, S, h->det != 0, h->lo.idx16, sh.grid, sh.block, sh.smem, h->s, a));
+    CU(launch_walk(kernel_lattice(h), S, h->det != 0, h->lo.idx16, sh.grid, sh.block, sh.smem, h->s, a));
     CU(launch_summary(h->d_st, h->lo.nlines, h->budget, h->d_flags, h->d_summary, h->s));
     CU(cudaMemcpyAsync(h->h_summary, h->d_summary, sizeof(Summary), cudaMemcpyDeviceToHost, h->s));
     return WL_OK;
@@ -473,7 +506,13 @@ wl_status run_slice(wl_ctx* h, int S, const Shape& sh, bool use_graph)
         h->launches += 2;
         return WL_OK;
     }
-    if (!h->graph || h->graph_S != S || h->graph_stage != sh.stage) {
+    WalkArgs now = base_args(h);
+    now.stage_smem = sh.stage;
+    now.slot_bytes = sh.slot;
+    const bool same = h->graph && h->graph_S == S && h->graph_stage == sh.stage &&
+                      h->graph_grid == sh.grid.x && h->graph_block == sh.block.x &&
+                      memcmp(&h->graph_args, &now, sizeof now) == 0;
+    if (!same) {
         if (h->graph) cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
         cudaGraph_t g;
@@ -487,6 +526,9 @@ wl_status run_slice(wl_ctx* h, int S, const Shape& sh, bool use_graph)
         if (e != cudaSuccess) return fail(WL_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
         h->graph_S = S;
         h->graph_stage = sh.stage;
+        h->graph_grid = sh.grid.x;
+        h->graph_block = sh.block.x;
+        memcpy(&h->graph_args, &now, sizeof now);
     }
     CU(cudaGraphLaunch(h->graph, h->s));
     h->launches += 2;
@@ -505,6 +547,14 @@ wl_status check_flags(wl_ctx* h, const Summary& sm)
         return fail(WL_ETIMEOUT, "device deadline reached");
     }
     return WL_OK;
+}
+
+// Walker specialisation: the square lattice with L a power of two takes the
+// shift-and-mask geometry.
+int kernel_lattice(const wl_ctx* h)
+{
+    if (h->g.type == WL_SQUARE && (h->g.L & (h->g.L - 1)) == 0) return kSquareP2;
+    return h->g.type;
 }
 
 int pick_mapping_default(const wl_ctx* h)
@@ -607,9 +657,11 @@ wl_status run_plain(wl_ctx* h)
         h->pool.push_back(st);
     }
     const size_t isz = h->lo.idx16 ? 2 : 4;
-    const size_t slot = (size_t)h->lo.pstride * isz + (size_t)h->lo.W * 4;
-    const int stage = (kTableBytes + slot <= std::min<size_t>(h->max_smem, 200 * 1024) && slot <= 64 * 1024) ? 1 : 0;
-    const size_t smem = kTableBytes + (stage ? slot : 0);
+    const size_t stg = (size_t)h->lo.pstride * isz + (size_t)h->lo.W * 4;
+    const int stage = (kTableBytes + kWinBytes + stg <= std::min<size_t>(h->max_smem, 220 * 1024) &&
+                       stg <= 64 * 1024) ? 1 : 0;
+    const size_t slot = kWinBytes + (stage ? stg : 0);
+    const size_t smem = kTableBytes + slot;
     CU(cudaMemsetAsync(h->d_qheads, 0, h->lo.nlines * 4, h->s));
     CU(cudaEventRecord(h->ev_join, h->s));
     for (auto st : h->pool) CU(cudaStreamWaitEvent(st, h->ev_join, 0));
@@ -632,7 +684,7 @@ wl_status run_plain(wl_ctx* h)
             a.order = h->d_ident + l;
             a.qnext = h->d_qheads + l;
             cudaStream_t st = h->pool[issued % npool];
-            CU(launch_walk(h->g.type, S, h->det != 0, h->lo.idx16, dim3(1), dim3(S), smem, st, a));
+            CU(launch_walk(kernel_lattice(h), S, h->det != 0, h->lo.idx16, dim3(1), dim3(S), smem, st, a));
             ++issued;
         }
         for (auto st : h->pool) {
@@ -707,7 +759,7 @@ wl_status wl_set_option(wl_handle h, const char* key, int64_t v)
     } else if (k == "deterministic") {
         h->det = v ? 1 : 0;
     } else if (k == "check_interval") {
-        if (v < 1) return fail(WL_EINVAL, "check_interval must be >= 1");
+        if (v < 1 || v > 0x7FFFFFFFll) return fail(WL_EINVAL, "check_interval must be in [1, 2^31-1]");
         h->C = v;
     } else if (k == "move_budget") {
         if (v < 0) return fail(WL_EINVAL, "move_budget must be >= 0");
@@ -913,6 +965,7 @@ wl_status wl_get_stats(wl_handle h, wl_stats* out)
         out->moves += s.t;
         out->accepts += s.accepts;
         out->checks += s.checks;
+        out->batches += s.batches;
         out->lines_converged += s.status == 1;
         out->min_stage = std::min<int32_t>(out->min_stage, (int32_t)s.stage);
         out->max_stage = std::max<int32_t>(out->max_stage, (int32_t)s.stage);

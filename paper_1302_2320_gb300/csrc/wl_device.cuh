@@ -13,7 +13,13 @@ constexpr uint32_t kVisited = 0x80000000u;   // hist word: bit 31 = bin ever vis
 constexpr int kTableN = 4096;
 constexpr int kTableBytes = kTableN * 4;     // entries 1..4095 as u32; entry 0 is 2^32
 
-enum LatticeType : int { kSquare = 0, kTriangular = 1, kCubic = 2 };
+// kSquareP2: the square lattice when L is a power of two (coordinates by
+// shift and mask); the same lattice and bond set as kSquare.
+enum LatticeType : int { kSquare = 0, kTriangular = 1, kCubic = 2, kSquareP2 = 3 };
+
+// Per-walker window of ln g (int64) and histogram (u32) bins in shared memory.
+constexpr int kWin = 64;
+constexpr int kWinBytes = kWin * 12;
 
 // Per-line scalar state (device, one per walked line).
 struct LineState {
@@ -25,6 +31,7 @@ struct LineState {
     int64_t t_stage;   // t at the start of the current stage
     int64_t status;    // 0 running, 1 converged, 2 histogram overflow, 3 invariant broken
     int64_t checks;    // flatness checks made
+    int64_t batches;   // speculative batches evaluated (diagnostic)
 };
 
 struct LineDesc {
@@ -36,6 +43,8 @@ struct LineDesc {
 struct Geo {
     int type, L, N, NB, W;   // W = 32-bit words of packed spins per line (multiple of 4)
     uint64_t magic;          // ceil(2^40 / L): x / L == (x * magic) >> 40 for x < 2^24
+    int lshift;              // log2(L) when L is a power of two
+    uint32_t lmask;          // L - 1 when L is a power of two
 };
 
 // Everything a walker launch needs.  Pointers are device memory.
@@ -56,7 +65,7 @@ struct WalkArgs {
     uint32_t seed;
     int32_t flat_pm;         // flatness fraction x in 1/1000
     int32_t stage_smem;      // 1: lists and spins staged in shared memory
-    int32_t slot_bytes;      // shared bytes per walker slot when staged
+    int32_t slot_bytes;      // shared bytes per walker slot (window + staged list/spins)
     int32_t pstride;         // list entries per line, N rounded up to 16 bytes
     int64_t C;               // flatness check interval
     int64_t budget;          // per-line cap on t
@@ -102,7 +111,14 @@ template <int LAT>
 __device__ __forceinline__ void neighbours(const Geo& g, uint32_t i, uint32_t* nb)
 {
     const uint32_t L = (uint32_t)g.L;
-    if (LAT == kCubic) {
+    if (LAT == kSquareP2) {
+        const uint32_t x = i & g.lmask, yrow = i & ~g.lmask;
+        const uint32_t rowL = (uint32_t)g.N - L;      // offset of the last row
+        nb[0] = yrow | ((x + 1) & g.lmask);
+        nb[1] = yrow | ((x - 1) & g.lmask);
+        nb[2] = (yrow == rowL ? 0u : yrow + L) | x;
+        nb[3] = (yrow == 0u ? rowL : yrow - L) | x;
+    } else if (LAT == kCubic) {
         const uint32_t r = divL(g, i), x = i - r * L;
         const uint32_t zc = divL(g, r), y = r - zc * L;
         const uint32_t xp = x + 1 == L ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;
@@ -130,7 +146,9 @@ __device__ __forceinline__ void neighbours(const Geo& g, uint32_t i, uint32_t* n
     }
 }
 
-template <int LAT> struct Coord { static constexpr int z = LAT == kSquare ? 4 : 6; };
+template <int LAT> struct Coord {
+    static constexpr int z = (LAT == kSquare || LAT == kSquareP2) ? 4 : 6;
+};
 
 // Change of k when up-spin i and down-spin j are exchanged.  With u_i, u_j the
 // up neighbours of i and j in the current configuration and a_ij the number
@@ -163,13 +181,18 @@ __device__ __forceinline__ bool accept_uphill(int64_t d, uint32_t r, const uint3
                                               float neg_u_log2e)
 {
     if (DET) {
-        const uint64_t i = (uint64_t)d >> q;
-        if (i >= (uint64_t)(kTableN - 1)) return false;
+        // branch-free: d <= 0 or past the table gives an index that is clamped
+        // (the caller ignores the result for d <= 0)
+        const uint64_t iu = (uint64_t)d >> q;
+        const bool in = d > 0 && iu < (uint64_t)(kTableN - 1);
+        const uint32_t i = in ? (uint32_t)iu : 0u;
+        // t0 - t1 < 2^32 and the fraction < 2^q <= 2^30: one 32x32->64 product
+        const uint32_t t1 = tab[i + 1];
         const uint64_t t0 = i == 0 ? (1ull << 32) : (uint64_t)tab[i];
-        const uint64_t t1 = (uint64_t)tab[i + 1];
-        const uint64_t fr = (uint64_t)d & ((1ull << q) - 1ull);
-        const uint64_t T = t0 - (((t0 - t1) * fr) >> q);
-        return (uint64_t)r < T;
+        const uint32_t diff = (uint32_t)(t0 - t1);
+        const uint32_t fr = (uint32_t)d & ((1u << q) - 1u);
+        const uint64_t T = t0 - (((uint64_t)diff * fr) >> q);
+        return in && (uint64_t)r < T;
     } else {
         const float p = exp2f((float)d * neg_u_log2e);
         return (float)(r >> 8) * 0x1p-24f < p;

@@ -81,6 +81,7 @@ __global__ void init_kernel(const InitArgs A)
         s.t_stage = 0;
         s.status = 0;
         s.checks = 0;
+        s.batches = 0;
         if (ell == 0) {
             hist[s.k >> 1] = kVisited;
             s.F = 0;
@@ -277,15 +278,16 @@ cudaError_t launch_philox(size_t n, const uint32_t* ctr, const uint32_t* key, ui
 __global__ void summary_kernel(const LineState* st, int nlines, int64_t budget,
                                const int32_t* flags, Summary* out)
 {
-    __shared__ long long s_moves[32], s_acc[32], s_chk[32];
+    __shared__ long long s_moves[32], s_acc[32], s_chk[32], s_bat[32];
     __shared__ int s_active[32], s_conv[32], s_ovf[32], s_min[32], s_max[32];
-    long long moves = 0, acc = 0, chk = 0;
+    long long moves = 0, acc = 0, chk = 0, bat = 0;
     int active = 0, conv = 0, ovf = 0, mn = INT_MAX, mx = 0;
     for (int i = threadIdx.x; i < nlines; i += blockDim.x) {
         const LineState s = st[i];
         moves += s.t;
         acc += s.accepts;
         chk += s.checks;
+        bat += s.batches;
         active += (s.status == 0 && s.t < budget);
         conv += (s.status == 1);
         ovf += (s.status == 2);
@@ -296,6 +298,7 @@ __global__ void summary_kernel(const LineState* st, int nlines, int64_t budget,
         moves += __shfl_xor_sync(0xffffffffu, moves, off);
         acc += __shfl_xor_sync(0xffffffffu, acc, off);
         chk += __shfl_xor_sync(0xffffffffu, chk, off);
+        bat += __shfl_xor_sync(0xffffffffu, bat, off);
         active += __shfl_xor_sync(0xffffffffu, active, off);
         conv += __shfl_xor_sync(0xffffffffu, conv, off);
         ovf += __shfl_xor_sync(0xffffffffu, ovf, off);
@@ -307,6 +310,7 @@ __global__ void summary_kernel(const LineState* st, int nlines, int64_t budget,
         s_moves[w] = moves;
         s_acc[w] = acc;
         s_chk[w] = chk;
+        s_bat[w] = bat;
         s_active[w] = active;
         s_conv[w] = conv;
         s_ovf[w] = ovf;
@@ -315,11 +319,12 @@ __global__ void summary_kernel(const LineState* st, int nlines, int64_t budget,
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        Summary r = {0, 0, 0, 0, 0, 0, INT_MAX, 0, 0};
+        Summary r = {0, 0, 0, 0, 0, 0, 0, INT_MAX, 0, 0};
         for (int x = 0; x < (int)(blockDim.x >> 5); ++x) {
             r.moves += s_moves[x];
             r.accepts += s_acc[x];
             r.checks += s_chk[x];
+            r.batches += s_bat[x];
             r.active += s_active[x];
             r.converged += s_conv[x];
             r.overflow += s_ovf[x];
@@ -353,6 +358,8 @@ cudaError_t launch_walk(int lattice, int S, bool det, bool idx16, dim3 grid, dim
                         size_t smem, cudaStream_t s, const WalkArgs& a)
 {
     if (lattice == kSquare) return launch_walk_square(S, det, idx16, grid, block, smem, s, a, nullptr);
+    if (lattice == kSquareP2)
+        return launch_walk_square_p2(S, det, idx16, grid, block, smem, s, a, nullptr);
     if (lattice == kTriangular)
         return launch_walk_triangular(S, det, idx16, grid, block, smem, s, a, nullptr);
     return launch_walk_cubic(S, det, idx16, grid, block, smem, s, a, nullptr);
@@ -364,6 +371,8 @@ cudaError_t walk_kernel_attrs(int lattice, int S, bool det, bool idx16, size_t s
     WalkArgs dummy{};
     const dim3 z(0), b(block_threads);
     if (lattice == kSquare) return launch_walk_square(S, det, idx16, z, b, smem, 0, dummy, blocks_per_sm);
+    if (lattice == kSquareP2)
+        return launch_walk_square_p2(S, det, idx16, z, b, smem, 0, dummy, blocks_per_sm);
     if (lattice == kTriangular)
         return launch_walk_triangular(S, det, idx16, z, b, smem, 0, dummy, blocks_per_sm);
     return launch_walk_cubic(S, det, idx16, z, b, smem, 0, dummy, blocks_per_sm);

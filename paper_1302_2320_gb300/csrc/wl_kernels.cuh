@@ -24,7 +24,7 @@ struct InitArgs {
 };
 
 struct Summary {
-    int64_t moves, accepts, checks;
+    int64_t moves, accepts, checks, batches;
     int32_t active, converged, overflow, min_stage, max_stage, flags;
 };
 
@@ -43,6 +43,8 @@ cudaError_t launch_walk_triangular(int S, bool det, bool idx16, dim3 grid, dim3 
                                    cudaStream_t s, const WalkArgs& a, int* bps);
 cudaError_t launch_walk_cubic(int S, bool det, bool idx16, dim3 grid, dim3 block, size_t smem,
                               cudaStream_t s, const WalkArgs& a, int* bps);
+cudaError_t launch_walk_square_p2(int S, bool det, bool idx16, dim3 grid, dim3 block, size_t smem,
+                                  cudaStream_t s, const WalkArgs& a, int* bps);
 
 cudaError_t launch_init(int lattice, bool idx16, const InitArgs& a, cudaStream_t s);
 cudaError_t launch_assemble(const LineDesc* desc, const int64_t* lng, const uint32_t* hist, int N,

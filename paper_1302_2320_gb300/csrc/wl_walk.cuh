@@ -73,125 +73,215 @@ __device__ void group_stage_step(int64_t* lng, uint32_t* hist, int nbins, int m,
     __syncwarp(gmask);
 }
 
+// Window of ln g / histogram bins a walker keeps in shared memory.  Every
+// proposal lies within z bins of the current bin (|dk| <= 2z), so the window
+// [wb, wb + kWin) is re-centred whenever the current bin comes within z bins of
+// an edge that is not the line's own edge.
+
+template <int S>
+__device__ __forceinline__ void window_store(int64_t* wl, uint32_t* wh, int64_t* lng, uint32_t* hist,
+                                             int wb, int wn, int m)
+{
+    for (int x = m; x < wn; x += S) {
+        lng[wb + x] = wl[x];
+        hist[wb + x] = wh[x];
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void window_load(int64_t* wl, uint32_t* wh, const int64_t* lng,
+                                            const uint32_t* hist, int wb, int wn, int m)
+{
+    for (int x = m; x < wn; x += S) {
+        wl[x] = lng[wb + x];
+        wh[x] = hist[wb + x];
+    }
+}
+
+__device__ __forceinline__ int window_base(int bc, int nbins)
+{
+    int wb = bc - kWin / 2;
+    if (wb > nbins - kWin) wb = nbins - kWin;
+    return wb < 0 ? 0 : wb;
+}
+
+__device__ __forceinline__ uint4 philox_step(uint64_t t, uint2 key)
+{
+    return philox4x32_10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), 0u, 0u), key);
+}
+
 // Walk line `li` for up to A.slice_moves moves (or to its budget, or to
-// convergence).  perm/sp point at the line's list and spins, in shared or
-// global memory.  All lanes of the group hold identical copies of the scalar
-// state.
+// convergence).  perm/sp point at the line's list and spins (shared or global
+// memory); win is the group's window (kWin int64 ln g, then kWin u32 hist).
+// All lanes of the group hold identical copies of the scalar state.  The
+// current bin's ln g, histogram word and pending count live in registers and
+// are authoritative; every other bin is up to date in the window (inside it)
+// or in global memory (outside it).
+//
+// Random numbers are double-buffered: lane m holds Philox(t + m) in (r0x, r0y,
+// r0z) and Philox(t + S + m) in (r1x, r1y, r1z).  After a batch commits c
+// steps the buffers are shifted by c with two shuffles, and the lanes whose
+// entry falls past the buffered range draw Philox(t + c + S + m) -- a value
+// the next batch does not use, so its latency overlaps the next batch's work.
 template <int LAT, int S, bool DET, typename IDX>
 __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned gmask,
-                          IDX* perm, uint32_t* sp, const uint32_t* tab)
+                          IDX* perm, uint32_t* sp, const uint32_t* tab, uint8_t* win)
 {
+    constexpr int zb = Coord<LAT>::z;     // largest bin step of one move
     const LineDesc D = A.desc[li];
     LineState* P = A.st + li;
     int64_t k = P->k, t = P->t, F = P->F, stage = P->stage, accepts = P->accepts;
     int64_t t_stage = P->t_stage, status = P->status, checks = P->checks;
+    int64_t batches = P->batches;
     if (status != 0) return;
-    const int ell = D.ell;
+    const int ell = D.ell, nbins = D.nbins;
     const uint32_t nd = (uint32_t)(A.g.N - ell);
     int64_t* lng = A.lng + D.bin_off;
     uint32_t* hist = A.hist + D.bin_off;
+    int64_t* wl = reinterpret_cast<int64_t*>(win);
+    uint32_t* wh = reinterpret_cast<uint32_t*>(win + kWin * 8);
     const uint2 key = make_uint2((uint32_t)ell, A.seed);
     int64_t end = t + A.slice_moves;
     if (end > A.budget) end = A.budget;
 
     int bc = (int)(k >> 1);
-    int64_t cur = lng[bc];
-    uint32_t hcur = hist[bc];
+    int wb = window_base(bc, nbins);
+    const int wn = nbins < kWin ? nbins : kWin;
+    window_load<S>(wl, wh, lng, hist, wb, wn, m);
+    __syncwarp(gmask);
+    int64_t cur = wl[bc - wb];
+    uint32_t hcur = wh[bc - wb];
     uint32_t pend = 0;
+    int64_t mF = (int64_t)m * F;          // ln g added at k by m earlier rejections
     int stop = 0;
+
+    uint4 r0 = philox_step((uint64_t)(t + m), key);
+    uint4 r1 = make_uint4(0u, 0u, 0u, 0u);
+    uint64_t tf = (uint64_t)(t + S + m);   // pending draw for r1
+    bool needf = true;
 
     while (t < end && !stop) {
         const int64_t next_check = (t / A.C + 1) * A.C;
-        int64_t lim64 = next_check - t;
-        if (end - t < lim64) lim64 = end - t;
-        const int lim = lim64 < S ? (int)lim64 : S;
+        const int64_t seg_end = next_check < end ? next_check : end;
+        int left = (int)(seg_end - t);    // moves before the next check or the slice end
 
-        bool acc = false, bad = false;
-        uint32_t a = 0, b = 0, i = 0, j = 0;
-        int kp = (int)k;
-        int64_t lp = 0;
-        if (m < lim) {
-            const uint64_t tt = (uint64_t)(t + m);
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)tt, (uint32_t)(tt >> 32), 0u, 0u), key);
-            a = pick(r.x, (uint32_t)ell);
-            b = pick(r.y, nd);
-            i = (uint32_t)perm[a];
-            j = (uint32_t)perm[ell + b];
-            kp = (int)k + delta_k<LAT>(A.g, sp, i, j);
-            if (kp == (int)k) {
-                acc = true;
-            } else if ((unsigned)(kp >> 1) >= (unsigned)D.nbins) {
-                bad = true;      // k' outside the line's bins: state invariant broken
-            } else {
-                lp = lng[kp >> 1];
-                const int64_t d = lp - (cur + (int64_t)m * F);
-                acc = d <= 0 || accept_uphill<DET>(d, r.z, tab, A.q, A.neg_u_log2e);
+        while (left > 0) {
+            const int lim = left < S ? left : S;
+            // the pending draw (independent of this batch's loads)
+            const uint4 rf = philox_step(tf, key);
+            // evaluate step t + m from the current state (branch-free)
+            const uint32_t a = pick(r0.x, (uint32_t)ell);
+            const uint32_t b = pick(r0.y, nd);
+            const uint32_t i = (uint32_t)perm[a];
+            const uint32_t j = (uint32_t)perm[ell + b];
+            const int kp = (int)k + delta_k<LAT>(A.g, sp, i, j);
+            const int wx = (kp >> 1) - wb;
+            const bool inb = (unsigned)(kp >> 1) < (unsigned)nbins && (unsigned)wx < (unsigned)wn;
+            const bool same = kp == (int)k;
+            const int64_t lp = wl[inb ? wx : 0];
+            const int64_t d = lp - cur - mF;
+            const bool up = accept_uphill<DET>(d, r0.z, tab, A.q, A.neg_u_log2e);
+            const bool act = m < lim;
+            const bool acc = act && (same || (inb && (d <= 0 || up)));
+            const bool bad = act && !same && !inb;   // k' outside its bins or the window
+            if (needf) r1 = rf;
+            if (__ballot_sync(gmask, bad)) {
+                stop = 4;
+                break;
             }
-        }
-        if (__ballot_sync(gmask, bad)) {
-            stop = 4;
-            break;
-        }
-        unsigned bal = __ballot_sync(gmask, acc);
-        if constexpr (S < 32) bal = (bal >> gbase) & ((1u << S) - 1u);
-        if (bal) {
-            const int ms = __ffs(bal) - 1;
-            const int src = gbase + ms;
-            const int kn = __shfl_sync(gmask, kp, src);
-            const int64_t ln = __shfl_sync(gmask, lp, src);
-            if (m == ms) {
-                perm[a] = (IDX)j;
-                perm[ell + b] = (IDX)i;
-                sp[i >> 5] &= ~(1u << (i & 31u));
-                sp[j >> 5] |= 1u << (j & 31u);
-            }
-            accepts += 1;
-            if (kn != (int)k) {
-                const uint32_t pt = pend + (uint32_t)ms;
-                if (pt) {
-                    if ((uint64_t)(hcur & ~kVisited) + pt >= (uint64_t)kVisited) stop = 2;
-                    if (m == 0) {
-                        lng[bc] = cur + (int64_t)ms * F;
-                        hist[bc] = (hcur + pt) | kVisited;
+            unsigned bal = __ballot_sync(gmask, acc);
+            if constexpr (S < 32) bal = (bal >> gbase) & ((1u << S) - 1u);
+            const int c = bal ? __ffs(bal) : lim;      // steps committed by this batch
+            if (bal) {
+                const int ms = c - 1;
+                const int src = gbase + ms;
+                const int kn = __shfl_sync(gmask, kp, src);
+                const int64_t ln = __shfl_sync(gmask, lp, src);
+                if (m == ms) {
+                    perm[a] = (IDX)j;
+                    perm[ell + b] = (IDX)i;
+                    sp[i >> 5] &= ~(1u << (i & 31u));
+                    sp[j >> 5] |= 1u << (j & 31u);
+                }
+                accepts += 1;
+                if (kn != (int)k) {
+                    const uint32_t pt = pend + (uint32_t)ms;
+                    if (pt) {
+                        if ((uint64_t)(hcur & ~kVisited) + pt >= (uint64_t)kVisited) stop = 2;
+                        if (m == 0) {
+                            wl[bc - wb] = cur + (int64_t)ms * F;
+                            wh[bc - wb] = (hcur + pt) | kVisited;
+                        }
                     }
+                    k = kn;
+                    bc = kn >> 1;
+                    cur = ln + F;
+                    hcur = wh[bc - wb];
+                    pend = 1;
+                    if ((bc - zb < wb && wb > 0) || (bc + zb >= wb + kWin && wb + kWin < nbins)) {
+                        // re-centre the window (the current bin stays in registers)
+                        __syncwarp(gmask);
+                        window_store<S>(wl, wh, lng, hist, wb, wn, m);
+                        __syncwarp(gmask);
+                        wb = window_base(bc, nbins);
+                        window_load<S>(wl, wh, lng, hist, wb, wn, m);
+                    }
+                } else {
+                    cur += (int64_t)c * F;
+                    pend += (uint32_t)c;
                 }
-                k = kn;
-                bc = kn >> 1;
-                cur = ln + F;
-                hcur = hist[bc];
-                pend = 1;
+                __syncwarp(gmask);
             } else {
-                cur += (int64_t)(ms + 1) * F;
-                pend += (uint32_t)(ms + 1);
+                cur += (int64_t)lim * F;
+                pend += (uint32_t)lim;
             }
-            t += ms + 1;
-            __syncwarp(gmask);
-        } else {
-            cur += (int64_t)lim * F;
-            pend += (uint32_t)lim;
-            t += lim;
+            // shift the random-number buffers by c: lane m now needs steps
+            // t + c + m (r0) and t + c + S + m (r1)
+            {
+                const int srcm = m + c;                       // < 2S
+                const int sl = gbase + (srcm & (S - 1));
+                const uint32_t ax = __shfl_sync(gmask, r0.x, sl), ay = __shfl_sync(gmask, r0.y, sl),
+                               az = __shfl_sync(gmask, r0.z, sl);
+                const uint32_t bx = __shfl_sync(gmask, r1.x, sl), by = __shfl_sync(gmask, r1.y, sl),
+                               bz = __shfl_sync(gmask, r1.z, sl);
+                needf = srcm >= S;
+                r0 = needf ? make_uint4(bx, by, bz, 0u) : make_uint4(ax, ay, az, 0u);
+                r1 = make_uint4(bx, by, bz, 0u);
+                tf = (uint64_t)(t + c + S + m);
+            }
+            t += c;
+            left -= c;
+            batches += 1;
+            if (stop) break;
         }
-        if ((hcur & ~kVisited) + (uint64_t)pend >= (uint64_t)kVisited) stop = 2;
+        if (stop) break;
 
-        if (t == next_check && !stop) {
-            // flush the current bin, then test flatness over the line
-            if (pend) {
-                hcur = (hcur + pend) | kVisited;
-                if (m == 0) {
-                    lng[bc] = cur;
-                    hist[bc] = hcur;
-                }
-                pend = 0;
+        if (t == next_check) {
+            // current bin -> window -> global, then test flatness over the line
+            if ((uint64_t)(hcur & ~kVisited) + pend >= (uint64_t)kVisited) {
+                stop = 2;
+                break;
             }
+            if (pend) hcur = (hcur + pend) | kVisited;
+            pend = 0;
+            if (m == 0) {
+                wl[bc - wb] = cur;
+                wh[bc - wb] = hcur;
+            }
+            __syncwarp(gmask);
+            window_store<S>(wl, wh, lng, hist, wb, wn, m);
             __syncwarp(gmask);
             checks += 1;
-            if (group_flat<S>(hist, D.nbins, m, gmask, A.flat_pm)) {
-                group_stage_step<S>(lng, hist, D.nbins, m, gmask);
+            if (group_flat<S>(hist, nbins, m, gmask, A.flat_pm)) {
+                group_stage_step<S>(lng, hist, nbins, m, gmask);
                 F >>= 2;                     // ln f -> ln f / 4
+                mF = (int64_t)m * F;
                 stage += 1;
                 t_stage = t;
-                cur = lng[bc];
-                hcur = hist[bc];
+                window_load<S>(wl, wh, lng, hist, wb, wn, m);
+                __syncwarp(gmask);
+                cur = wl[bc - wb];
+                hcur = wh[bc - wb];
                 if (F == 0) {                // ln f < ln f_min
                     status = 1;
                     break;
@@ -208,12 +298,15 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
             if (req) stop = req;
         }
     }
-    if (pend) {
-        hcur = (hcur + pend) | kVisited;
+    // current bin -> window -> global
+    if (stop != 4) {
+        if (pend) hcur = (hcur + pend) | kVisited;
         if (m == 0) {
-            lng[bc] = cur;
-            hist[bc] = hcur;
+            wl[bc - wb] = cur;
+            wh[bc - wb] = hcur;
         }
+        __syncwarp(gmask);
+        window_store<S>(wl, wh, lng, hist, wb, wn, m);
     }
     if (stop == 2) status = 2;
     if (stop == 4) status = 3;
@@ -226,6 +319,7 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
         P->t_stage = t_stage;
         P->status = status;
         P->checks = checks;
+        P->batches = batches;
         if (stop == 1) atomicOr(A.flags, 1);
         if (stop == 3) atomicOr(A.flags, 2);
         if (stop == 2) atomicOr(A.flags, 4);
@@ -265,7 +359,10 @@ __global__ void walk_kernel(const WalkArgs A)
     const int gbase = lane - m;
     const unsigned gmask = group_mask<S>(gbase);
     const int gid = threadIdx.x / S;
+    // per-group slot: window, then (when staged) the list and the spins
     uint8_t* slot = smem + kTableBytes + (size_t)gid * (size_t)A.slot_bytes;
+    uint8_t* win = slot;
+    slot += kWinBytes;
     // per-line strides are padded to 16 bytes: pstride list entries, W spin words
     const int pstride = A.pstride, W = A.g.W;
     const int perm_words = (int)((size_t)pstride * sizeof(IDX) / 4);
@@ -286,13 +383,13 @@ __global__ void walk_kernel(const WalkArgs A)
                           perm_words, m);
             group_copy<S>(ssp, gsp, W, m);
             __syncwarp(gmask);
-            walk_line<LAT, S, DET, IDX>(A, li, m, gbase, gmask, sperm, ssp, tab);
+            walk_line<LAT, S, DET, IDX>(A, li, m, gbase, gmask, sperm, ssp, tab, win);
             group_copy<S>(reinterpret_cast<uint32_t*>(gperm), reinterpret_cast<const uint32_t*>(sperm),
                           perm_words, m);
             group_copy<S>(gsp, ssp, W, m);
             __syncwarp(gmask);
         } else {
-            walk_line<LAT, S, DET, IDX>(A, li, m, gbase, gmask, gperm, gsp, tab);
+            walk_line<LAT, S, DET, IDX>(A, li, m, gbase, gmask, gperm, gsp, tab, win);
         }
     }
 }
