@@ -159,6 +159,42 @@ wl_status wl_philox(size_t n, const uint32_t* ctr, const uint32_t* key, uint32_t
 
 wl_status wl_destroy(wl_handle h);
 
+/* The batched walker for callers that cannot allocate device memory.  The
+ * paper has no counterpart; this is a deployment variant.  Some callers cannot
+ * call cudaMalloc -- while another framework owns the device's memory pool,
+ * where an allocation (or the synchronisation cudaMalloc/cudaFree may imply)
+ * is not allowed, or under a memory plan fixed up front -- but can own every
+ * input and output buffer.  This call allocates nothing: its scratch (exp
+ * tables, line descriptors, work queue, control words, run summary) is one
+ * fixed ~129 KB __device__ array inside the library, held by every GPU that
+ * loads it until the process exits.
+ *
+ * Walks lines ell_first .. ell_first+nlines-1 (all <= N/2; nlines <= 4096, the
+ * scratch limit -- larger requests return WL_EINVAL before any launch) of the
+ * periodic lattice, exactly as wl_run does with the same options (seed,
+ * deterministic, check_interval, move_budget, mapping; 0 = 8 lanes per walker),
+ * on `stream` (a cudaStream_t as an integer, 0 = default stream), and returns
+ * when every line converged (WL_OK) or reached move_budget (WL_ENOTCONVERGED).
+ * init != 0 first initialises every line (as the first wl_run does); init == 0
+ * continues the state held in the buffers.  Caller-owned DEVICE buffers:
+ *   perm   nlines x P list entries, P = N rounded up so a line spans a multiple
+ *          of 16 bytes; uint16 entries if N <= 65536, else uint32; 16-byte aligned
+ *   spins  nlines x W uint32 words, W = ceil(N/32) rounded up to a multiple of 4
+ *   lng    int64, hist uint32: the lines' bins back to back, line l holding
+ *          min(z*min(l, N-l), N_B)/2 + 1 bins (k = 0, 2, ...)
+ *   state  nlines x 9 int64: k, t, F, stage, accepts, t at stage start,
+ *          status, checks, batches
+ * The first call on a device looks up the scratch address (cudaGetSymbolAddress),
+ * so make one call before any stream capture.  Every call shares the scratch
+ * and resets its control words; calls whose work overlaps on the GPU (from
+ * several threads or streams) race on it and must be serialised by the caller.
+ * Errors as for wl_run; the message is in wl_last_error(). */
+wl_status wl_walk_noalloc(wl_lattice lattice, int L, int ell_first, int nlines, uint32_t seed,
+                          int deterministic, double ln_f_min, double flatness,
+                          int64_t check_interval, int64_t move_budget, int mapping, int init,
+                          void* perm, uint32_t* spins, int64_t* lng, uint32_t* hist,
+                          int64_t* state, int64_t stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* wl_last_error(void);
 

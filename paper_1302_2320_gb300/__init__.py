@@ -33,7 +33,7 @@ WL_OK, WL_ENOTCONVERGED, WL_ETIMEOUT, WL_EABORTED = 0, 6, 4, 5
 EXPORTED = ["wl_create", "wl_required_bytes", "wl_set_option", "wl_get_option", "wl_run",
             "wl_abort", "wl_reset", "wl_assemble", "wl_get_lng", "wl_get_surface",
             "wl_get_stats", "wl_get_line_state", "wl_get_exp_table", "wl_philox", "wl_destroy",
-            "wl_last_error"]
+            "wl_last_error", "wl_walk_noalloc"]
 
 
 class WLError(RuntimeError):

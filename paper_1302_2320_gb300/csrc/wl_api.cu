@@ -161,6 +161,11 @@ std::map<TuneKey, int> g_tune_cache;
 
 }  // namespace
 
+namespace wl {
+// Lets other translation units of the library report through wl_last_error().
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace wl
+
 struct wl_ctx {
     LatInfo g{};
     Layout lo;
