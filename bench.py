@@ -34,7 +34,7 @@ LN_F_MIN = 1e-6
 FLATNESS = 0.8
 CHECK_INTERVAL = 16384
 MOVES_PER_LINE = 1 << 22
-INT_OPS_PER_MOVE = 124      # algorithmic 32-bit integer operations per move attempt
+INT_OPS_PER_MOVE = 136      # algorithmic 32-bit integer operations per move attempt (square lattice)
 
 
 def _peaks():
@@ -107,6 +107,23 @@ def _dist():
     return world, rank, local
 
 
+def rank_seed(rank: int) -> int:
+    """Each rank walks its own surface replica: seeds never overlap across ranks."""
+    return 1000 * (rank + 1)
+
+
+def combine_ranks(dist, total_ms, e2e_sec, moves, e2e_moves, device=None):
+    """Max over ranks of the timings, sum over ranks of the work (moves)."""
+    import torch
+    if not dist:
+        return float(total_ms), float(e2e_sec), float(moves), float(e2e_moves)
+    mx = torch.tensor([total_ms, e2e_sec], dtype=torch.float64, device=device)
+    sm = torch.tensor([moves, e2e_moves], dtype=torch.float64, device=device)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(mx[1]), float(sm[0]), float(sm[1])
+
+
 def _cpu_sample(ells, budget, seed, threads):
     """Oracle (deterministic mode, as it stands) on a bounded sample of lines."""
     import oracle
@@ -174,7 +191,7 @@ def run_ours(args):
 
     h = wl.Handle(LATTICE, L, deterministic=1, check_interval=CHECK_INTERVAL,
                   move_budget=args.moves_per_line, slice_moves=args.moves_per_line,
-                  mapping=args.mapping, stream=stream.cuda_stream)
+                  mapping=args.mapping, form=args.form, stream=stream.cuda_stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
 
     def step(seed):
@@ -183,7 +200,7 @@ def run_ours(args):
         h.run(LN_F_MIN, FLATNESS)
         h.assemble()
 
-    seed0 = 1000 * (rank + 1)
+    seed0 = rank_seed(rank)
     for w in range(max(args.warmup, 1)):
         step(seed0 + w)
     mapping = h.stats()["mapping"]
@@ -229,14 +246,7 @@ def run_ours(args):
         e2e_moves += h.stats()["moves"]
     clk = clocks.stop() if rank == 0 else None
 
-    vals = torch.tensor([total_ms, e2e_sec, float(moves), float(e2e_moves)], dtype=torch.float64)
-    if dist:
-        mx = vals[:2].clone().to(dev)
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = vals[2:].clone().to(dev)
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        vals = torch.cat([mx.cpu(), sm.cpu()])
-    total_ms, e2e_sec, moves, e2e_moves = [float(x) for x in vals]
+    total_ms, e2e_sec, moves, e2e_moves = combine_ranks(dist, total_ms, e2e_sec, moves, e2e_moves, dev)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -283,7 +293,7 @@ def run_ours(args):
                                f"{args.moves_per_line} moves/line/step, deterministic",
                    "lattice": LATTICE, "L": L, "lines": N // 2 + 1, "ln_f_min": LN_F_MIN,
                    "check_interval": CHECK_INTERVAL, "moves_per_line": args.moves_per_line,
-                   "form": "persistent", "mapping": mapping,
+                   "form": "persistent" if args.form == 0 else "one launch per line", "mapping": mapping,
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
@@ -312,7 +322,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--moves-per-line", type=int, default=MOVES_PER_LINE)
     ap.add_argument("--mapping", type=int, default=0)
-    ap.add_argument("--cpu-moves", type=int, default=20_000_000)
+    ap.add_argument("--cpu-moves", type=int, default=150_000_000)
+    ap.add_argument("--form", type=int, default=0, help="0 persistent batched, 1 one launch per line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

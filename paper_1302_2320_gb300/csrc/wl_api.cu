@@ -655,7 +655,7 @@ wl_status run_plain(wl_ctx* h)
 {
     int S = h->mapping ? h->mapping : pick_mapping_default(h);
     h->last_mapping = S;
-    const int npool = 16;
+    const int npool = 128;      // the device runs at most 128 kernels at once
     while ((int)h->pool.size() < npool) {
         cudaStream_t st;
         CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));

@@ -173,6 +173,25 @@ __device__ __forceinline__ int delta_k(const Geo& g, const uint32_t* sp, uint32_
     return 2 * (ui - uj + a);
 }
 
+// delta_k that also returns the neighbour lists of i and j (used to decide
+// which later proposals an accepted exchange of i and j can affect).
+template <int LAT>
+__device__ __forceinline__ int delta_k_nb(const Geo& g, const uint32_t* sp, uint32_t i, uint32_t j,
+                                          uint32_t* ni, uint32_t* nj)
+{
+    constexpr int z = Coord<LAT>::z;
+    neighbours<LAT>(g, i, ni);
+    neighbours<LAT>(g, j, nj);
+    int ui = 0, uj = 0, a = 0;
+#pragma unroll
+    for (int m = 0; m < z; ++m) {
+        ui += (int)spin_at(sp, ni[m]);
+        uj += (int)spin_at(sp, nj[m]);
+        a += (int)(ni[m] == j);
+    }
+    return 2 * (ui - uj + a);
+}
+
 // Eq. 3 for an uphill move of d > 0 units of u.
 //  deterministic: accept iff r < T(d), T linearly interpolated in the table
 //  production:    accept iff U24(r) < 2^(-d u log2 e) in FP32

@@ -152,7 +152,6 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
     int64_t cur = wl[bc - wb];
     uint32_t hcur = wh[bc - wb];
     uint32_t pend = 0;
-    int64_t mF = (int64_t)m * F;          // ln g added at k by m earlier rejections
     int stop = 0;
 
     uint4 r0 = philox_step((uint64_t)(t + m), key);
@@ -167,73 +166,105 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
 
         while (left > 0) {
             const int lim = left < S ? left : S;
-            // the pending draw (independent of this batch's loads)
+            // the pending draw (independent of this batch)
             const uint4 rf = philox_step(tf, key);
-            // evaluate step t + m from the current state (branch-free)
+            // -- parallel phase: lane m proposes step t + m against the state at
+            //    the start of the batch (list slots a, b, sites i, j, their
+            //    neighbours and the change of k)
             const uint32_t a = pick(r0.x, (uint32_t)ell);
             const uint32_t b = pick(r0.y, nd);
             const uint32_t i = (uint32_t)perm[a];
             const uint32_t j = (uint32_t)perm[ell + b];
-            const int kp = (int)k + delta_k<LAT>(A.g, sp, i, j);
-            const int wx = (kp >> 1) - wb;
-            const bool inb = (unsigned)(kp >> 1) < (unsigned)nbins && (unsigned)wx < (unsigned)wn;
-            const bool same = kp == (int)k;
-            const int64_t lp = wl[inb ? wx : 0];
-            const int64_t d = lp - cur - mF;
-            const bool up = accept_uphill<DET>(d, r0.z, tab, A.q, A.neg_u_log2e);
-            const bool act = m < lim;
-            const bool acc = act && (same || (inb && (d <= 0 || up)));
-            const bool bad = act && !same && !inb;   // k' outside its bins or the window
+            uint32_t ni[zb], nj[zb];
+            const int dk = delta_k_nb<LAT>(A.g, sp, i, j, ni, nj);
             if (needf) r1 = rf;
-            if (__ballot_sync(gmask, bad)) {
-                stop = 4;
-                break;
-            }
-            unsigned bal = __ballot_sync(gmask, acc);
-            if constexpr (S < 32) bal = (bal >> gbase) & ((1u << S) - 1u);
-            const int c = bal ? __ffs(bal) : lim;      // steps committed by this batch
-            if (bal) {
-                const int ms = c - 1;
-                const int src = gbase + ms;
-                const int kn = __shfl_sync(gmask, kp, src);
-                const int64_t ln = __shfl_sync(gmask, lp, src);
-                if (m == ms) {
-                    perm[a] = (IDX)j;
-                    perm[ell + b] = (IDX)i;
-                    sp[i >> 5] &= ~(1u << (i & 31u));
-                    sp[j >> 5] |= 1u << (j & 31u);
+            // -- serial phase: the steps in order with Eq. 3 against the current
+            //    k and ln g.  An accepted exchange of (i_s, j_s) leaves a later
+            //    proposal exact unless it reuses list slot a_s or b_s or one of
+            //    i_s, j_s neighbours its sites; such proposals are marked, and the
+            //    batch ends at the first marked one.
+            unsigned inv = 0u, accm = 0u;
+            int c = lim;
+            for (int s = 0; s < lim; ++s) {
+                const int src = gbase + s;
+                const int dks = __shfl_sync(gmask, dk, src);
+                const uint32_t rzs = __shfl_sync(gmask, r0.z, src);
+                if ((inv >> s) & 1u) {
+                    c = s;
+                    break;
                 }
-                accepts += 1;
-                if (kn != (int)k) {
-                    const uint32_t pt = pend + (uint32_t)ms;
-                    if (pt) {
-                        if ((uint64_t)(hcur & ~kVisited) + pt >= (uint64_t)kVisited) stop = 2;
-                        if (m == 0) {
-                            wl[bc - wb] = cur + (int64_t)ms * F;
-                            wh[bc - wb] = (hcur + pt) | kVisited;
-                        }
+                const int kp = (int)k + dks;
+                bool acc = true;
+                int64_t lp = 0;
+                if (dks != 0) {
+                    const int bp = kp >> 1;
+                    const int wx = bp - wb;
+                    if ((unsigned)bp >= (unsigned)nbins) {      // invariant broken
+                        stop = 4;
+                        c = s;
+                        break;
                     }
-                    k = kn;
-                    bc = kn >> 1;
-                    cur = ln + F;
+                    if ((unsigned)wx >= (unsigned)wn) {        // walked off the window
+                        c = s;
+                        break;
+                    }
+                    lp = wl[wx];
+                    const int64_t d = lp - cur;
+                    acc = d <= 0 || accept_uphill<DET>(d, rzs, tab, A.q, A.neg_u_log2e);
+                }
+                if (!acc) {
+                    cur += F;
+                    pend += 1u;
+                    continue;
+                }
+                accm |= 1u << s;
+                if (dks != 0) {
+                    // leave the current bin: its ln g and histogram go to the window
+                    if ((uint64_t)(hcur & ~kVisited) + pend >= (uint64_t)kVisited) stop = 2;
+                    if (pend) hcur = (hcur + pend) | kVisited;
+                    wl[bc - wb] = cur;
+                    wh[bc - wb] = hcur;
+                    k = kp;
+                    bc = kp >> 1;
+                    cur = lp + F;
                     hcur = wh[bc - wb];
-                    pend = 1;
-                    if ((bc - zb < wb && wb > 0) || (bc + zb >= wb + kWin && wb + kWin < nbins)) {
-                        // re-centre the window (the current bin stays in registers)
-                        __syncwarp(gmask);
-                        window_store<S>(wl, wh, lng, hist, wb, wn, m);
-                        __syncwarp(gmask);
-                        wb = window_base(bc, nbins);
-                        window_load<S>(wl, wh, lng, hist, wb, wn, m);
-                    }
+                    pend = 1u;
                 } else {
-                    cur += (int64_t)c * F;
-                    pend += (uint32_t)c;
+                    cur += F;
+                    pend += 1u;
                 }
+                // later proposals that the accepted exchange of (i_s, j_s) affects
+                const uint32_t as = __shfl_sync(gmask, a, src), bs = __shfl_sync(gmask, b, src);
+                const uint32_t is = __shfl_sync(gmask, i, src), js = __shfl_sync(gmask, j, src);
+                bool conf = (a == as) | (b == bs);
+#pragma unroll
+                for (int q = 0; q < zb; ++q)
+                    conf |= (ni[q] == is) | (ni[q] == js) | (nj[q] == is) | (nj[q] == js);
+                unsigned cb = __ballot_sync(gmask, conf && m > s);
+                if constexpr (S < 32) cb = (cb >> gbase) & ((1u << S) - 1u);
+                inv |= cb;
+                if (stop) {
+                    c = s + 1;
+                    break;
+                }
+            }
+            if (c == 0) stop = 4;                  // lane 0 is always evaluable
+            // apply the accepted exchanges (mutually independent) to lists and spins
+            if ((accm >> m) & 1u) {
+                perm[a] = (IDX)j;
+                perm[ell + b] = (IDX)i;
+                atomicAnd(&sp[i >> 5], ~(1u << (i & 31u)));
+                atomicOr(&sp[j >> 5], 1u << (j & 31u));
+            }
+            accepts += __popc(accm);
+            __syncwarp(gmask);
+            if ((bc - zb < wb && wb > 0) || (bc + zb >= wb + kWin && wb + kWin < nbins)) {
+                // re-centre the window (the current bin stays in registers)
+                window_store<S>(wl, wh, lng, hist, wb, wn, m);
                 __syncwarp(gmask);
-            } else {
-                cur += (int64_t)lim * F;
-                pend += (uint32_t)lim;
+                wb = window_base(bc, nbins);
+                window_load<S>(wl, wh, lng, hist, wb, wn, m);
+                __syncwarp(gmask);
             }
             // shift the random-number buffers by c: lane m now needs steps
             // t + c + m (r0) and t + c + S + m (r1)
@@ -275,7 +306,6 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
             if (group_flat<S>(hist, nbins, m, gmask, A.flat_pm)) {
                 group_stage_step<S>(lng, hist, nbins, m, gmask);
                 F >>= 2;                     // ln f -> ln f / 4
-                mF = (int64_t)m * F;
                 stage += 1;
                 t_stage = t;
                 window_load<S>(wl, wh, lng, hist, wb, wn, m);
