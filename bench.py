@@ -107,6 +107,169 @@ def _dist():
     return world, rank, local
 
 
+KERNEL_SOURCES = ["paper_1302_2320_gb300/csrc/wl_walk.cuh", "paper_1302_2320_gb300/csrc/wl_device.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "walk_kernel_L64_traffic.txt")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def walker_traffic(moves_per_line: int, mapping: int):
+    """DRAM bytes of one benchmark walk launch from the committed ncu summary,
+    or None when it was taken on another launch shape or an older kernel."""
+    try:
+        fields = {}
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    fields[k.strip()] = v.strip()
+        if (fields.get("kernel_source_sha256") == kernel_source_hash()
+                and int(fields.get("moves_per_line", -1)) == moves_per_line
+                and int(fields.get("mapping", -1)) == mapping):
+            return int(fields["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
+def run_converge(args):
+    """Time to ln f_min: one whole surface walked until every line converged
+    (or the time limit), reported as its own JSON line."""
+    import paper_1302_2320_gb300 as wl
+    wl.build()
+    lat, Lc = args.lattice, args.converge
+    h = wl.Handle(lat, Lc, deterministic=1, check_interval=args.check_interval, seed=1,
+                  mapping=args.mapping, timeout_ms=int(args.time_limit * 1000),
+                  same_f_resets=args.same_f_resets)
+    t0 = time.perf_counter()
+    rc = h.run(args.ln_f_min, FLATNESS, allow=(wl.WL_OK, wl.WL_ETIMEOUT))
+    sec = time.perf_counter() - t0
+    st = h.stats()
+    line = {"mode": "time_to_ln_f_min", "lattice": lat, "L": Lc, "N": h.N, "lines": st["lines"],
+            "ln_f_min": args.ln_f_min, "check_interval": args.check_interval,
+            "same_f_resets": args.same_f_resets,
+            "status": "converged" if rc == wl.WL_OK else "time limit",
+            "seconds": sec, "lines_converged": st["lines_converged"],
+            "min_stage": st["min_stage"], "max_stage": st["max_stage"], "moves": st["moves"],
+            "moves_per_s": st["moves"] / sec, "mapping": st["mapping"],
+            "accept_rate": st["accepts"] / max(st["moves"], 1)}
+    print(json.dumps(line), flush=True)
+    h.close()
+    return 0
+
+
+SERVE_MIX = [("square", 16), ("square", 24), ("square", 32), ("square", 48),
+             ("triangular", 16), ("triangular", 32), ("cubic", 6), ("cubic", 8)]
+
+
+def run_serve(args):
+    """Serving: a Poisson stream of DOS requests through the continuous-batching
+    loop; p50/p99 time-to-DOS (submit -> assembled surface in host memory) and
+    aggregate moves/s."""
+    import numpy as np
+    import paper_1302_2320_gb300 as wl
+    wl.build()
+    rng = np.random.default_rng(2024)
+    n = args.serve
+    kinds = [SERVE_MIX[i] for i in rng.integers(0, len(SERVE_MIX), n)]
+    us = rng.choice([1e-6, 1e-7], n)
+    budget = args.serve_moves
+    # calibrate: each lattice once alone -> mean service time
+    srv = wl.Server(hbm_budget=args.hbm_budget, max_active=args.max_active)
+    solo = {}
+    for lat, L in SERVE_MIX:
+        t0 = time.perf_counter()
+        rid = srv.submit(lat, L, seed=7, ln_f_min=1e-6, check_interval=args.check_interval,
+                         move_budget=budget)
+        srv.wait(rid)
+        solo[(lat, L)] = time.perf_counter() - t0
+        srv.release(rid)
+    mean_solo = float(np.mean([solo[k] for k in kinds]))
+    lam = args.load * args.max_active / mean_solo          # requests per second
+    gaps = rng.exponential(1.0 / lam, n)
+    ids, t_start = [], time.perf_counter()
+    t_next = t_start
+    for x in range(n):
+        t_next += gaps[x]
+        while time.perf_counter() < t_next:
+            time.sleep(min(0.002, max(0.0, t_next - time.perf_counter())))
+        lat, L = kinds[x]
+        ids.append(srv.submit(lat, L, seed=100 + x, ln_f_min=float(us[x]),
+                              check_interval=args.check_interval, move_budget=budget))
+    lat_s, moves, fails = [], 0, 0
+    for rid in ids:
+        rc = srv.wait(rid)
+        info = srv.info(rid)
+        fails += info["state"] != 2
+        lat_s.append(info["finish_s"] - info["submit_s"])
+        moves += info["moves"]
+        srv.release(rid)
+    span = time.perf_counter() - t_start
+    srv.close()
+    lat_s = np.array(lat_s)
+    line = {"mode": "serving", "requests": n, "failed": int(fails),
+            "p50_time_to_dos_s": float(np.percentile(lat_s, 50)),
+            "p99_time_to_dos_s": float(np.percentile(lat_s, 99)),
+            "mean_time_to_dos_s": float(lat_s.mean()), "makespan_s": span,
+            "aggregate_moves_per_s": moves / span, "offered_load": args.load,
+            "arrival_rate_per_s": lam, "max_active": args.max_active, "hbm_budget": args.hbm_budget,
+            "move_budget_per_line": budget, "check_interval": args.check_interval,
+            "mix": [f"{lat} L={L}" for lat, L in SERVE_MIX], "ln_f_min": [1e-6, 1e-7],
+            "solo_seconds": {f"{lat} L={L}": v for (lat, L), v in solo.items()}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_accuracy(args):
+    """Accuracy of the 12x12 surface against the exact transfer-matrix values
+    (tests/golden/square_L12_exact.txt): seeds walked concurrently, production
+    mode, to ln f_min; mean and max |d ln g_kl| inside and at the two ends of
+    each line's spectrum."""
+    import numpy as np
+    from concurrent.futures import ThreadPoolExecutor
+    import paper_1302_2320_gb300 as wl
+    wl.build()
+    exact = {}
+    for ell, k, lg in np.loadtxt(os.path.join(ROOT, "tests", "golden", "square_L12_exact.txt")):
+        exact.setdefault(int(ell), {})[int(k)] = float(lg)
+
+    def one(seed):
+        h = wl.Handle("square", 12, seed=seed, deterministic=0, check_interval=args.check_interval,
+                      timeout_ms=int(args.time_limit * 1000))
+        t0 = time.perf_counter()
+        rc = h.run(args.ln_f_min, FLATNESS, allow=(wl.WL_OK, wl.WL_ETIMEOUT))
+        sec = time.perf_counter() - t0
+        h.assemble()
+        return rc, sec, h.stats()["moves"], [h.get_lng(ell) for ell in range(73)]
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(args.seeds) as ex:
+        res = list(ex.map(one, range(1, args.seeds + 1)))
+    inner, ends = [], []
+    for rc, _, _, lines in res:
+        for ell in range(73):
+            ks = sorted(exact[ell])
+            for k in ks:
+                d = abs(lines[ell][k // 2] - exact[ell][k])
+                (ends if k in (ks[0], ks[-1]) and len(ks) > 2 else inner).append(d)
+    inner, ends = np.array(inner), np.array(ends)
+    print(json.dumps({"mode": "accuracy_square_L12", "ln_f_min": args.ln_f_min, "seeds": args.seeds,
+                      "check_interval": args.check_interval, "production": True,
+                      "converged_seeds": sum(r[0] == wl.WL_OK for r in res),
+                      "seconds_per_seed": [r[1] for r in res], "wall_s": time.perf_counter() - t0,
+                      "inner_mean": float(inner.mean()), "inner_max": float(inner.max()),
+                      "ends_mean": float(ends.mean()), "ends_max": float(ends.max()),
+                      "all_mean": float(np.concatenate([inner, ends]).mean())}), flush=True)
+    return 0
+
+
 def rank_seed(rank: int) -> int:
     """Each rank walks its own surface replica: seeds never overlap across ranks."""
     return 1000 * (rank + 1)
@@ -124,13 +287,13 @@ def combine_ranks(dist, total_ms, e2e_sec, moves, e2e_moves, device=None):
     return float(mx[0]), float(mx[1]), float(sm[0]), float(sm[1])
 
 
-def _cpu_sample(ells, budget, seed, threads):
+def _cpu_sample(ells, budget, seed, threads, Lc=L):
     """Oracle (deterministic mode, as it stands) on a bounded sample of lines."""
     import oracle
     from concurrent.futures import ThreadPoolExecutor
 
     def one(ell):
-        st = oracle.run_line(oracle.SQUARE, L, ell, seed, LN_F_MIN, CHECK_INTERVAL,
+        st = oracle.run_line(oracle.SQUARE, Lc, ell, seed, LN_F_MIN, CHECK_INTERVAL,
                              int(FLATNESS * 1000), budget, 0)
         return st.t
     t0 = time.perf_counter()
@@ -187,6 +350,7 @@ def run_ours(args):
     wl.build()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    L = args.L
     N = L * L
 
     h = wl.Handle(LATTICE, L, deterministic=1, check_interval=CHECK_INTERVAL,
@@ -211,7 +375,7 @@ def run_ours(args):
         clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    moves = launches = 0
+    moves = launches = accepts = batches = 0
     walk_ms = 0.0
     if dist:
         dist.barrier()
@@ -223,6 +387,8 @@ def run_ours(args):
         ev[s][1].record(stream)
         st = h.stats()
         moves += st["moves"]
+        accepts += st["accepts"]
+        batches += st["batches"]
         walk_ms += st["walk_ms"]
         launches += st["launches"] + 1           # + the assembly kernel
     torch.cuda.synchronize()
@@ -260,23 +426,14 @@ def run_ours(args):
     per_rank_moves = moves / world
     walk_s = walk_ms / 1000.0
     achieved = per_rank_moves * INT_OPS_PER_MOVE / walk_s / 1e12
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "walk_kernel_traffic.json")
-    if os.path.exists(tfile):
-        try:
-            with open(tfile) as f:
-                tj = json.load(f)
-            if tj.get("moves_per_line") == args.moves_per_line and tj.get("L") == L:
-                traffic = tj.get("dram_bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = walker_traffic(args.moves_per_line, mapping) if L == 64 else None
 
     cpu = None
     if not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         ells = [N // 8, N // 4, 3 * N // 8, N // 2]
         ells = (ells * ((threads + 3) // 4))[:max(threads, 4)]
-        m, sec = _cpu_sample(ells, args.cpu_moves, 1, threads)
+        m, sec = _cpu_sample(ells, args.cpu_moves, 1, threads, L)
         cpu = {"value": m / sec, "unit": "moves/s", "cores": threads, "kind": "oracle",
                "sample": f"{args.cpu_moves} moves on each of {len(ells)} walks of lines "
                          f"N/8, N/4, 3N/8, N/2 (deterministic, C={CHECK_INTERVAL}), {sec:.1f} s"}
@@ -306,6 +463,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
         "walk_ms_per_step": walk_ms / args.steps,
+        "accept_rate": accepts / max(moves, 1), "moves_per_batch": moves / max(batches, 1),
     }
     print(json.dumps(line), flush=True)
     h.close()
@@ -321,11 +479,32 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--moves-per-line", type=int, default=MOVES_PER_LINE)
+    ap.add_argument("--L", type=int, default=L, help="square lattice size (default 64)")
     ap.add_argument("--mapping", type=int, default=0)
     ap.add_argument("--cpu-moves", type=int, default=150_000_000)
     ap.add_argument("--form", type=int, default=0, help="0 persistent batched, 1 one launch per line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--converge", type=int, default=0,
+                    help="walk a whole LxL surface to ln f_min and report the time instead")
+    ap.add_argument("--lattice", default="square")
+    ap.add_argument("--ln-f-min", type=float, default=LN_F_MIN)
+    ap.add_argument("--check-interval", type=int, default=CHECK_INTERVAL)
+    ap.add_argument("--time-limit", type=float, default=600.0, help="seconds, --converge only")
+    ap.add_argument("--same-f-resets", type=int, default=0, help="extra same-f resets per stage")
+    ap.add_argument("--serve", type=int, default=0, help="run the serving benchmark with N requests")
+    ap.add_argument("--serve-moves", type=int, default=1 << 22, help="per-line move budget of a request")
+    ap.add_argument("--max-active", type=int, default=8)
+    ap.add_argument("--hbm-budget", type=int, default=32 << 30)
+    ap.add_argument("--load", type=float, default=0.8)
+    ap.add_argument("--accuracy", action="store_true", help="12x12 accuracy against the exact surface")
+    ap.add_argument("--seeds", type=int, default=8)
     args = ap.parse_args()
+    if args.accuracy:
+        return run_accuracy(args)
+    if args.serve:
+        return run_serve(args)
+    if args.converge:
+        return run_converge(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

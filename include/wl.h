@@ -46,14 +46,17 @@ typedef enum {
     WL_ENOTCONVERGED = 6,  /* "move_budget" reached before every line converged  */
     WL_EMISMATCH = 7,      /* device exp table differs from the host-built table */
     WL_ESTATE = 8,         /* call not valid in the handle's current state       */
-    WL_EOVERFLOW = 9       /* a histogram bin would exceed 2^31-1 within a stage */
+    WL_EOVERFLOW = 9       /* a histogram bin would exceed 2^63-1 within a stage */
 } wl_status;
 
-/* Periodic lattices.  Square: site i = y*L + x, neighbours (x+-1, y), (x, y+-1).
+/* Lattices.  Square: site i = y*L + x, neighbours (x+-1, y), (x, y+-1), periodic.
  * Triangular: rhombic LxL torus, the square's neighbours plus (x+1, y-1) and
- * (x-1, y+1).  Simple cubic: i = (z*L + y)*L + x, +-1 along each axis.
- * L >= 3 (no double bonds); N <= 2^20. */
-typedef enum { WL_SQUARE = 0, WL_TRIANGULAR = 1, WL_SIMPLE_CUBIC = 2 } wl_lattice;
+ * (x-1, y+1).  Simple cubic: i = (z*L + y)*L + x, +-1 along each axis,
+ * periodic.  Square with open boundaries (Fig. 2): the square lattice without
+ * the wrap-around bonds, N_B = 2L(L-1).  L >= 3 (no double bonds); N <= 2^20.
+ * On the periodic lattices k is always even (bins k = 0, 2, 4, ...); with open
+ * boundaries every k occurs (bins k = 0, 1, 2, ...). */
+typedef enum { WL_SQUARE = 0, WL_TRIANGULAR = 1, WL_SIMPLE_CUBIC = 2, WL_SQUARE_OPEN = 3 } wl_lattice;
 
 /* Aggregate counters of a handle (totals over lines l <= N/2). */
 typedef struct {
@@ -73,9 +76,9 @@ typedef struct {
     double assemble_ms;       /* device time of the last wl_assemble            */
 } wl_stats;
 
-/* Create a handle for an L x L (square, triangular) or L^3 (cubic) periodic
- * lattice (Eq. 1, "arbitrary lattice").  Computes the line table (bins of
- * the even k in [0, min(z*min(l, N-l), N_B)], Eq. 2's k range per line);
+/* Create a handle for an L x L (square, triangular, open square) or L^3
+ * (cubic) lattice (Eq. 1, "arbitrary lattice").  Computes the line table (bins
+ * of the k in [0, min(z*min(l, N-l), N_B)], Eq. 2's k range per line);
  * device memory is allocated at the first wl_run.  *out receives the handle.
  * Errors: WL_EINVAL (bad lattice or L). */
 wl_status wl_create(wl_lattice lattice, int L, wl_handle* out);
@@ -98,8 +101,13 @@ size_t wl_required_bytes(wl_lattice lattice, int L);
  *   "timeout_ms"     wall-clock limit of one wl_run, 0 = none (default 0)
  *   "hbm_budget"     refuse to allocate more than this many bytes (default 0 = none)
  *   "ell_min", "ell_max"  walk only lines in [ell_min, ell_max] (defaults 0, N/2)
- * Setting "seed", "deterministic" or "check_interval" after a run requires
- * wl_reset().  Errors: WL_EINVAL (unknown key or bad value), WL_ESTATE. */
+ *   "same_f_resets"  R: within the first R flatness checks of each stage, a
+ *                    histogram that is not flat is reset and ln g normalised
+ *                    while ln f is kept -- the extra reset the paper remarks
+ *                    after Eq. 4 speeds the walk; its trigger is not given
+ *                    there, this is one choice (default 0: off)
+ * Setting "seed", "deterministic", "check_interval", "same_f_resets" or the
+ * line range after a run requires wl_reset().  Errors: WL_EINVAL (unknown key or bad value), WL_ESTATE. */
 wl_status wl_set_option(wl_handle h, const char* key, int64_t value);
 wl_status wl_get_option(wl_handle h, const char* key, int64_t* value);
 
@@ -127,7 +135,7 @@ wl_status wl_assemble(wl_handle h);
 
 /* Copy line ell (0..N; ell > N/2 is served by its mirror N-ell) of the last
  * wl_assemble into out[0..n), n = number of bins, bin b holding k = k_lo +
- * b*k_step (k_lo = 0, k_step = 2).  If cap < n nothing is copied, *n_out is
+ * b*k_step (k_lo = 0; k_step = 2 periodic, 1 open boundaries).  If cap < n nothing is copied, *n_out is
  * set and WL_EINVAL is returned.  Errors: WL_ESTATE before wl_assemble. */
 wl_status wl_get_lng(wl_handle h, int ell, double* out, size_t cap,
                      int* k_lo, int* k_step, size_t* n_out);
@@ -139,6 +147,14 @@ wl_status wl_get_surface(wl_handle h, double* out, size_t cap, int64_t* offsets,
                          size_t offsets_cap, size_t* n_out);
 
 wl_status wl_get_stats(wl_handle h, wl_stats* out);
+
+/* Thermodynamics from the assembled surface (the partition function of Eq. 2
+ * with the energy of Eq. 1, J = k_B = 1): for every temperature T[a] > 0 and
+ * field H[c], per spin, out[(a*nH + c)*6 + 0..5] = ln Z / N, <E>/N,
+ * C/N = (<E^2> - <E>^2) / (N T^2), <M>/N, <|M|>/N, chi/N = (<M^2> - <M>^2)/(N T),
+ * with M = 2l - N (l up spins; lines l > N/2 are their mirrors).  Host arrays.
+ * Needs wl_assemble over every line l = 0..N/2 (else WL_ESTATE).  FP64. */
+wl_status wl_thermo(wl_handle h, const double* T, int nT, const double* H, int nH, double* out);
 
 /* Full state of one line walker, in plain layouts: scal[8] = {k, t, F (ln f
  * in units of u), stage, accepts, t at stage start, status (0 running,
@@ -158,6 +174,45 @@ wl_status wl_get_exp_table(wl_handle h, uint64_t* table, int* q);
 wl_status wl_philox(size_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out);
 
 wl_status wl_destroy(wl_handle h);
+
+/* ---- Serving: density-of-states requests with continuous batching ----
+ * A server owns a scheduler thread on the device current at creation.
+ * Requests (one lattice each, walked as wl_run would, to ln_f_min or to
+ * move_budget) are admitted in arrival order while their device footprint
+ * (wl_required_bytes) fits hbm_budget (0 = no limit) and fewer than max_active
+ * are running; every admitted request keeps its walker state on the device and
+ * has one slice in flight on its own stream, so the walks of all admitted
+ * requests overlap on the GPU.  A finished request's assembled surface (l =
+ * 0..N/2, as wl_get_surface) is kept in host memory until released.  In
+ * deterministic mode each result is bit-identical to the same request run
+ * alone through wl_run/wl_assemble. */
+typedef struct wl_server_ctx* wl_server;
+
+typedef struct {
+    int32_t state;         /* 0 queued, 1 running, 2 done, 3 failed             */
+    int32_t status;        /* wl_status of a finished request                   */
+    int32_t lattice, L;
+    int64_t moves;         /* move attempts so far (updated after each slice)   */
+    int64_t bins;          /* bins of the stored result, once done              */
+    int64_t device_bytes;  /* device memory held while admitted                 */
+    double submit_s, start_s, finish_s;   /* seconds since wl_server_create; -1 if not yet */
+} wl_request_info;
+
+wl_status wl_server_create(int64_t hbm_budget, int max_active, wl_server* out);
+/* Queue a request; *id identifies it.  WL_ENOMEM if it alone exceeds the budget. */
+wl_status wl_server_submit(wl_server s, wl_lattice lattice, int L, uint32_t seed, double ln_f_min,
+                           double flatness, int64_t check_interval, int64_t move_budget,
+                           int64_t* id);
+wl_status wl_server_info(wl_server s, int64_t id, wl_request_info* info);
+/* Block until the request finished (its status) or timeout_s elapsed
+ * (WL_ETIMEOUT; timeout_s < 0 waits forever). */
+wl_status wl_server_wait(wl_server s, int64_t id, double timeout_s);
+/* Copy a finished request's surface; *n_out = bins (set even if cap is too small). */
+wl_status wl_server_result(wl_server s, int64_t id, double* out, size_t cap, size_t* n_out);
+/* Forget a finished request and its stored surface. */
+wl_status wl_server_release(wl_server s, int64_t id);
+/* Stop the scheduler; running requests are dropped. */
+wl_status wl_server_destroy(wl_server s);
 
 /* The batched walker for callers that cannot allocate device memory.  The
  * paper has no counterpart; this is a deployment variant.  Some callers cannot
@@ -180,8 +235,9 @@ wl_status wl_destroy(wl_handle h);
  *   perm   nlines x P list entries, P = N rounded up so a line spans a multiple
  *          of 16 bytes; uint16 entries if N <= 65536, else uint32; 16-byte aligned
  *   spins  nlines x W uint32 words, W = ceil(N/32) rounded up to a multiple of 4
- *   lng    int64, hist uint32: the lines' bins back to back, line l holding
- *          min(z*min(l, N-l), N_B)/2 + 1 bins (k = 0, 2, ...)
+ *   lng    int64, hist uint64 (count, bit 63 = bin ever visited): the lines'
+ *          bins back to back, line l holding min(z*min(l, N-l), N_B)/2 + 1 bins
+ *          (k = 0, 2, ...)
  *   state  nlines x 9 int64: k, t, F, stage, accepts, t at stage start,
  *          status, checks, batches
  * The first call on a device looks up the scratch address (cudaGetSymbolAddress),
@@ -192,7 +248,7 @@ wl_status wl_destroy(wl_handle h);
 wl_status wl_walk_noalloc(wl_lattice lattice, int L, int ell_first, int nlines, uint32_t seed,
                           int deterministic, double ln_f_min, double flatness,
                           int64_t check_interval, int64_t move_budget, int mapping, int init,
-                          void* perm, uint32_t* spins, int64_t* lng, uint32_t* hist,
+                          void* perm, uint32_t* spins, int64_t* lng, uint64_t* hist,
                           int64_t* state, int64_t stream);
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -26,8 +26,9 @@ _OUT = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-SQUARE, TRIANGULAR, CUBIC = 0, 1, 2
-LATTICE_NAMES = {"square": SQUARE, "triangular": TRIANGULAR, "cubic": CUBIC}
+SQUARE, TRIANGULAR, CUBIC, SQUARE_OPEN = 0, 1, 2, 3
+LATTICE_NAMES = {"square": SQUARE, "triangular": TRIANGULAR, "cubic": CUBIC,
+                 "square_open": SQUARE_OPEN}
 
 # scalar slots of a line state (same order as the C enum)
 SC_K, SC_T, SC_F, SC_STAGE, SC_ACCEPTS, SC_TSTAGE, SC_STATUS, SC_CHECKS = range(8)
@@ -63,15 +64,18 @@ def lib():
         L.or_exp_table.argtypes = [dbl, vp, vp]
         L.or_threshold_of.argtypes = [dbl, i64]
         L.or_threshold_of.restype = ctypes.c_uint64
+        L.or_lattice_kstep.argtypes = [i32]
         L.or_line_nbins.argtypes = [i32, i32, i32]
         L.or_line_nbins.restype = i64
-        L.or_line_run.argtypes = [i32, i32, i32, u32, dbl, i64, i32, i64, i32, i32,
+        L.or_line_run.argtypes = [i32, i32, i32, u32, dbl, i64, i32, i64, i32, i32, i32,
                                   vp, vp, vp, vp, vp, vp]
         L.or_line_audit.argtypes = [i32, i32, i32, vp, vp, i64]
         L.or_assemble.argtypes = [i32, i32, i64, vp, vp, dbl, vp]
         L.or_assemble.restype = None
         L.or_brute_force.argtypes = [i32, i32, vp]
         L.or_tm_square.argtypes = [i32, i32, vp, i32]
+        L.or_thermo.argtypes = [i32, i32, vp, vp, i32, vp, i32, vp, i32, vp]
+        L.or_thermo.restype = None
         _lib = L
     return _lib
 
@@ -113,6 +117,11 @@ def threshold(u: float, d: int) -> int:
     return int(lib().or_threshold_of(u, d))
 
 
+def kstep(lattice: int) -> int:
+    """Spacing of the reachable k: 2 on the periodic lattices, 1 with open boundaries."""
+    return int(lib().or_lattice_kstep(lattice))
+
+
 def line_nbins(lattice: int, L: int, ell: int) -> int:
     return int(lib().or_line_nbins(lattice, L, ell))
 
@@ -152,16 +161,18 @@ class LineState:
 
 def run_line(lattice: int, L: int, ell: int, seed: int, u: float, C: int,
              flat_pm: int = 800, budget: int = 2**62, mode: int = 0,
-             state: LineState | None = None) -> LineState:
+             state: LineState | None = None, same_f_resets: int = 0) -> LineState:
     """Run (or continue) the walk on line ``ell`` until F == 0 or t == budget.
 
     mode 0 = deterministic (table acceptance), 1 = production (double exp).
+    same_f_resets = R > 0 resets a histogram that is not flat at the first R
+    checks of each stage, keeping f (the extra reset remarked after Eq. 4).
     """
     init = state is None
     if init:
         state = LineState(lattice, L, ell)
     rc = lib().or_line_run(lattice, L, ell, seed & 0xFFFFFFFF, u, C, flat_pm, budget, mode,
-                           1 if init else 0, _p(state.perm), _p(state.spins), _p(state.sc),
+                           1 if init else 0, same_f_resets, _p(state.perm), _p(state.spins), _p(state.sc),
                            _p(state.lng), _p(state.hist), _p(state.visited))
     if rc:
         raise ValueError("or_line_run rejected its arguments")
@@ -203,3 +214,31 @@ def tm_square(L: int, ell_max: int | None = None, nthreads: int | None = None) -
     if lib().or_tm_square(L, ell_max, _p(g), nthreads):
         raise ValueError("bad TM arguments")
     return g
+
+
+THERMO_FIELDS = ("lnZ", "E", "C", "M", "absM", "chi")
+
+
+def thermo(N: int, NB: int, offsets, lng, T, H, kstep: int = 2) -> np.ndarray:
+    """Eq. 2 thermodynamics per spin over a (T, H) grid, shape (nT, nH, 6)."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    lng = np.ascontiguousarray(lng, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    out = np.zeros((T.size, H.size, 6), dtype=np.float64)
+    lib().or_thermo(N, NB, _p(offsets), _p(lng), kstep, _p(T), T.size, _p(H), H.size, _p(out))
+    return out
+
+
+def exact_surface(g: np.ndarray, step: int = 2):
+    """Ragged ln g over lines l = 0..N/2 (bins k = 0, step, ... up to the line's
+    largest k) from an exact table g[k, l]; -inf where g = 0."""
+    N = g.shape[1] - 1
+    offs, vals = [0], []
+    for l in range(N // 2 + 1):
+        col = g[:, l]
+        nb = int(np.nonzero(col)[0].max()) // step + 1
+        with np.errstate(divide="ignore"):
+            vals.append(np.log(col[0:step * nb:step]))
+        offs.append(offs[-1] + nb)
+    return np.array(offs, dtype=np.int64), np.concatenate(vals)

@@ -36,6 +36,7 @@
 #define OR_SQUARE 0
 #define OR_TRIANGULAR 1
 #define OR_CUBIC 2
+#define OR_SQUARE_OPEN 3      /* square lattice with open boundaries (Fig. 2) */
 
 #define OR_MAXZ 6
 #define OR_TABLE_N 4096
@@ -62,10 +63,13 @@ static int or_lat_make(or_lattice* lat, int type, int L)
     } else if (type == OR_CUBIC) {
         lat->N = L * L * L;
         lat->z = 6;
+    } else if (type == OR_SQUARE_OPEN) {
+        lat->N = L * L;
+        lat->z = 4;                          /* largest degree; edges have 3, corners 2 */
     } else {
         return -1;
     }
-    lat->NB = lat->N * lat->z / 2;
+    lat->NB = type == OR_SQUARE_OPEN ? 2 * L * (L - 1) : lat->N * lat->z / 2;
     return 0;
 }
 
@@ -76,6 +80,14 @@ static int or_lat_make(or_lattice* lat, int type, int L)
 static int or_neighbours(const or_lattice* lat, int i, int* nb)
 {
     int L = lat->L;
+    if (lat->type == OR_SQUARE_OPEN) {     /* no wrap: edge sites have fewer bonds */
+        int x = i % L, y = i / L, d = 0;
+        if (x + 1 < L) nb[d++] = i + 1;
+        if (x > 0) nb[d++] = i - 1;
+        if (y + 1 < L) nb[d++] = i + L;
+        if (y > 0) nb[d++] = i - L;
+        return d;
+    }
     if (lat->type == OR_CUBIC) {
         int x = i % L, y = (i / L) % L, zc = i / (L * L);
         int xp = (x + 1) % L, xm = (x + L - 1) % L;
@@ -225,10 +237,16 @@ uint64_t or_threshold_of(double u, int64_t d)
 /* One micromagnetic line: the Wang-Landau walk at fixed l.                  */
 /* ------------------------------------------------------------------------ */
 
-/* Bins hold the even k in [0, k_hi(l)], k_hi = min(z*min(l, N-l), N_B): no
- * more than z bonds per minority spin can be unhappy.  On these periodic
- * lattices every site has even degree, so k has the parity of z*l, i.e. k is
- * always even and the bin of k is k/2. */
+/* Spacing of the reachable k.  On the periodic lattices every site has even
+ * degree, so k has the parity of z*l: k is always even and the bin of k is
+ * k/2.  With open boundaries edge sites have odd degree and k takes every
+ * value: the bin of k is k. */
+static int or_kstep(int type) { return type == OR_SQUARE_OPEN ? 1 : 2; }
+
+int or_lattice_kstep(int type) { return or_kstep(type); }
+
+/* Bins hold k in [0, k_hi(l)] with the lattice's spacing, k_hi = min(z*min(l,
+ * N-l), N_B): no more than z bonds per minority spin can be unhappy. */
 int64_t or_line_nbins(int type, int L, int ell)
 {
     or_lattice lat;
@@ -237,7 +255,7 @@ int64_t or_line_nbins(int type, int L, int ell)
     int lm = ell < lat.N - ell ? ell : lat.N - ell;
     int64_t khi = (int64_t)lat.z * lm;
     if (khi > lat.NB) khi = lat.NB;
-    return khi / 2 + 1;
+    return khi / or_kstep(type) + 1;
 }
 
 /* Scalar state slots (int64), shared layout with the Python wrapper. */
@@ -285,7 +303,7 @@ static void or_line_init(const or_lattice* lat, int ell, uint32_t seed, double u
     sc[SC_F] = llround(1.0 / u);          /* ln f = 1 initially (f = e) */
     if (ell == 0 || ell == N) {
         /* No exchange move exists: the line has the single state k = 0. */
-        visited[sc[SC_K] / 2] = 1;
+        visited[sc[SC_K] / or_kstep(lat->type)] = 1;
         sc[SC_F] = 0;
         sc[SC_STATUS] = 1;
     }
@@ -326,8 +344,9 @@ static int or_is_flat(const int64_t* hist, const uint8_t* visited, int64_t nbins
             S += hist[b];
         }
     if (n == 0) return 0;
+    /* products can pass 2^63 on long stages: compare in 128-bit integers */
     for (int64_t b = 0; b < nbins; b++)
-        if (visited[b] && 1000 * n * hist[b] >= (int64_t)flat_pm * S) c++;
+        if (visited[b] && (__int128)1000 * n * hist[b] >= (__int128)flat_pm * S) c++;
     return 1000 * c >= (int64_t)flat_pm * n;
 }
 
@@ -337,7 +356,7 @@ static int or_is_flat(const int64_t* hist, const uint8_t* visited, int64_t nbins
  * init != 0 prepares the initial state first; otherwise the state passed in
  * is continued.  Returns 0, or -1 on bad arguments. */
 int or_line_run(int type, int L, int ell, uint32_t seed, double u, int64_t C, int flat_pm,
-                int64_t budget, int mode, int init,
+                int64_t budget, int mode, int init, int same_f_resets,
                 int32_t* perm, uint8_t* spins, int64_t* sc,
                 int64_t* lng, int64_t* hist, uint8_t* visited)
 {
@@ -351,6 +370,7 @@ int or_line_run(int type, int L, int ell, uint32_t seed, double u, int64_t C, in
     if (init) or_line_init(&lat, ell, seed, u, perm, spins, sc, lng, hist, visited, nbins);
 
     int N = lat.N;
+    const int ks = or_kstep(type);
     int32_t* U = perm;          /* up-spin list   */
     int32_t* D = perm + ell;    /* down-spin list */
     uint32_t key[2] = {(uint32_t)ell, seed};
@@ -368,7 +388,7 @@ int or_line_run(int type, int L, int ell, uint32_t seed, double u, int64_t C, in
         int64_t kp = k + or_delta_k(&lat, spins, i, j);
 
         /* Eq. 3: accept with probability min(g(k)/g(k'), 1). */
-        int64_t d = lng[kp / 2] - lng[k / 2];
+        int64_t d = lng[kp / ks] - lng[k / ks];
         int accept;
         if (d <= 0) {
             accept = 1;
@@ -389,7 +409,7 @@ int or_line_run(int type, int L, int ell, uint32_t seed, double u, int64_t C, in
 
         /* g(current) *= f, h(current) += 1 -- after an accept the current state
          * is the proposal, after a reject it is the old state. */
-        int64_t bc = sc[SC_K] / 2;
+        int64_t bc = sc[SC_K] / ks;
         lng[bc] += sc[SC_F];
         hist[bc] += 1;
         visited[bc] = 1;
@@ -397,7 +417,21 @@ int or_line_run(int type, int L, int ell, uint32_t seed, double u, int64_t C, in
 
         if (sc[SC_T] % C == 0) {
             sc[SC_CHECKS]++;
-            if (or_is_flat(hist, visited, nbins, flat_pm)) {
+            int flat = or_is_flat(hist, visited, nbins, flat_pm);
+            if (!flat && same_f_resets > 0 && (sc[SC_T] - sc[SC_TSTAGE]) / C <= same_f_resets) {
+                /* The extra reset at unchanged f (the remark after Eq. 4 on
+                 * spectrum ends): within the first same_f_resets checks of a
+                 * stage a histogram that is not flat is reset and ln g
+                 * normalised, f is kept. */
+                int64_t mn = INT64_MAX;
+                for (int64_t x = 0; x < nbins; x++)
+                    if (visited[x] && lng[x] < mn) mn = lng[x];
+                for (int64_t x = 0; x < nbins; x++) {
+                    if (visited[x]) lng[x] -= mn;
+                    hist[x] = 0;
+                }
+            }
+            if (flat) {
                 /* Histogram reset, normalization, f -> f^(1/4).  In fixed point
                  * the normalization of Eq. 4 is a constant shift of ln g; the
                  * exact integer shift that keeps the visited minimum at zero
@@ -642,4 +676,63 @@ int or_tm_square(int L, int ell_max, double* g, int nthreads)
     free(rep);
     free(mult);
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Thermodynamics from the density of states (Eq. 2): for each temperature  */
+/* T (J = 1, k_B = 1) and field H,                                           */
+/*   Z = sum_{k,l} g_kl exp(-E_kl / T),  E_kl = -(N_B - 2k) - H M,           */
+/* M = sum_i S_i = 2l - N for l up spins (Eq. 1; the field term printed with */
+/* Eq. 2 has the opposite sign, which only mirrors <M>).  Input: ln g over   */
+/* lines l = 0..N/2 (ragged, offsets of                                      */
+/* length N/2 + 2, bin b holding k = b*kstep, -inf where g = 0); line        */
+/* l > N/2 is line N - l.  Output per (T, H), row-major [iT][iH][6]:          */
+/*   ln Z / N, <E>/N, C/N = (<E^2> - <E>^2)/(N T^2), <M>/N, <|M|>/N,          */
+/*   chi/N = (<M^2> - <M>^2)/(N T).                                           */
+/* ------------------------------------------------------------------------ */
+
+void or_thermo(int N, int NB, const int64_t* offsets, const double* lng, int kstep,
+               const double* T, int nT, const double* H, int nH, double* out)
+{
+    int half = N / 2;
+    for (int a = 0; a < nT; a++)
+        for (int c = 0; c < nH; c++) {
+            double beta = 1.0 / T[a], h = H[c];
+            double mx = -INFINITY;
+            for (int l = 0; l <= N; l++) {
+                int src = l <= half ? l : N - l;
+                for (int64_t b = offsets[src]; b < offsets[src + 1]; b++) {
+                    if (isinf(lng[b])) continue;
+                    int64_t k = (b - offsets[src]) * kstep;
+                    double E = -(double)(NB - 2 * k) - h * (double)(2 * l - N);
+                    double x = lng[b] - beta * E;
+                    if (x > mx) mx = x;
+                }
+            }
+            double z = 0, e1 = 0, e2 = 0, m1 = 0, ma = 0, m2 = 0;
+            for (int l = 0; l <= N; l++) {
+                int src = l <= half ? l : N - l;
+                for (int64_t b = offsets[src]; b < offsets[src + 1]; b++) {
+                    if (isinf(lng[b])) continue;
+                    int64_t k = (b - offsets[src]) * kstep;
+                    double M = (double)(2 * l - N);
+                    double E = -(double)(NB - 2 * k) - h * M;
+                    double w = exp(lng[b] - beta * E - mx);
+                    z += w;
+                    e1 += w * E;
+                    e2 += w * E * E;
+                    m1 += w * M;
+                    ma += w * fabs(M);
+                    m2 += w * M * M;
+                }
+            }
+            e1 /= z; e2 /= z; m1 /= z; ma /= z; m2 /= z;
+            double* o = out + ((size_t)a * nH + c) * 6;
+            o[0] = (mx + log(z)) / N;
+            o[1] = e1 / N;
+            o[2] = (e2 - e1 * e1) * beta * beta / N;
+            o[3] = m1 / N;
+            o[4] = ma / N;
+            o[5] = (m2 - m1 * m1) * beta / N;
+        }
 }

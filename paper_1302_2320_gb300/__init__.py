@@ -23,8 +23,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libwl.so")
 
-WL_SQUARE, WL_TRIANGULAR, WL_SIMPLE_CUBIC = 0, 1, 2
-LATTICES = {"square": WL_SQUARE, "triangular": WL_TRIANGULAR, "cubic": WL_SIMPLE_CUBIC}
+WL_SQUARE, WL_TRIANGULAR, WL_SIMPLE_CUBIC, WL_SQUARE_OPEN = 0, 1, 2, 3
+LATTICES = {"square": WL_SQUARE, "triangular": WL_TRIANGULAR, "cubic": WL_SIMPLE_CUBIC,
+            "square_open": WL_SQUARE_OPEN}
 STATUS = {0: "WL_OK", 1: "WL_EINVAL", 2: "WL_ENOMEM", 3: "WL_ECUDA", 4: "WL_ETIMEOUT",
           5: "WL_EABORTED", 6: "WL_ENOTCONVERGED", 7: "WL_EMISMATCH", 8: "WL_ESTATE",
           9: "WL_EOVERFLOW"}
@@ -33,7 +34,9 @@ WL_OK, WL_ENOTCONVERGED, WL_ETIMEOUT, WL_EABORTED = 0, 6, 4, 5
 EXPORTED = ["wl_create", "wl_required_bytes", "wl_set_option", "wl_get_option", "wl_run",
             "wl_abort", "wl_reset", "wl_assemble", "wl_get_lng", "wl_get_surface",
             "wl_get_stats", "wl_get_line_state", "wl_get_exp_table", "wl_philox", "wl_destroy",
-            "wl_last_error", "wl_walk_noalloc"]
+            "wl_last_error", "wl_walk_noalloc", "wl_server_create", "wl_server_submit",
+            "wl_server_info", "wl_server_wait", "wl_server_result", "wl_server_release",
+            "wl_server_destroy", "wl_thermo"]
 
 
 class WLError(RuntimeError):
@@ -96,6 +99,14 @@ def lib():
         L.wl_destroy.argtypes = [vp]
         L.wl_last_error.argtypes = []
         L.wl_last_error.restype = cp
+        L.wl_thermo.argtypes = [vp, vp, i32, vp, i32, vp]
+        L.wl_server_create.argtypes = [i64, i32, vp]
+        L.wl_server_submit.argtypes = [vp, i32, i32, u32, dbl, dbl, i64, i64, vp]
+        L.wl_server_info.argtypes = [vp, i64, vp]
+        L.wl_server_wait.argtypes = [vp, i64, dbl]
+        L.wl_server_result.argtypes = [vp, i64, vp, sz, vp]
+        L.wl_server_release.argtypes = [vp, i64]
+        L.wl_server_destroy.argtypes = [vp]
         _lib = L
         return L
 
@@ -206,7 +217,8 @@ class Handle:
         return s.as_dict()
 
     def line_state(self, ell: int) -> dict:
-        nb = int(min(self.get_option("z") * min(ell, self.N - ell), self.NB) // 2 + 1)
+        nb = int(min(self.get_option("z") * min(ell, self.N - ell), self.NB)
+                 // self.get_option("k_step") + 1)
         d = {"sc": np.zeros(8, dtype=np.int64), "perm": np.zeros(self.N, dtype=np.int32),
              "spins": np.zeros(self.N, dtype=np.uint8), "lng": np.zeros(nb, dtype=np.int64),
              "hist": np.zeros(nb, dtype=np.int64), "visited": np.zeros(nb, dtype=np.uint8)}
@@ -215,8 +227,76 @@ class Handle:
                "wl_get_line_state")
         return d
 
+    def thermo(self, T, H) -> np.ndarray:
+        """Eq. 2 thermodynamics per spin, shape (len(T), len(H), 6): ln Z/N, E/N,
+        C/N, M/N, |M|/N, chi/N."""
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        H = np.ascontiguousarray(H, dtype=np.float64)
+        out = np.zeros((T.size, H.size, 6), dtype=np.float64)
+        _check(lib().wl_thermo(self._h, _p(T), T.size, _p(H), H.size, _p(out)), "wl_thermo")
+        return out
+
     def exp_table(self):
         t = np.zeros(4096, dtype=np.uint64)
         q = ctypes.c_int()
         _check(lib().wl_get_exp_table(self._h, _p(t), ctypes.byref(q)), "wl_get_exp_table")
         return t, q.value
+
+
+class wl_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("lattice", ctypes.c_int32),
+                ("L", ctypes.c_int32), ("moves", ctypes.c_int64), ("bins", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("submit_s", ctypes.c_double),
+                ("start_s", ctypes.c_double), ("finish_s", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Server:
+    """Continuous-batching request loop (wl_server_*): submit lattices, wait for
+    their assembled surfaces."""
+
+    def __init__(self, hbm_budget: int = 0, max_active: int = 16):
+        self._s = ctypes.c_void_p()
+        _check(lib().wl_server_create(int(hbm_budget), int(max_active), ctypes.byref(self._s)),
+               "wl_server_create")
+
+    def submit(self, lattice, L: int, seed: int = 1, ln_f_min: float = 1e-6, flatness: float = 0.8,
+               check_interval: int = 1000, move_budget: int = 2**62) -> int:
+        if isinstance(lattice, str):
+            lattice = LATTICES[lattice]
+        rid = ctypes.c_int64()
+        _check(lib().wl_server_submit(self._s, lattice, L, seed, ln_f_min, flatness, check_interval,
+                                      move_budget, ctypes.byref(rid)), "wl_server_submit")
+        return rid.value
+
+    def info(self, rid: int) -> dict:
+        i = wl_request_info()
+        _check(lib().wl_server_info(self._s, rid, ctypes.byref(i)), "wl_server_info")
+        return i.as_dict()
+
+    def wait(self, rid: int, timeout_s: float = -1.0) -> int:
+        return _check(lib().wl_server_wait(self._s, rid, timeout_s), "wl_server_wait",
+                      ok=(WL_OK, WL_ENOTCONVERGED, WL_ETIMEOUT))
+
+    def result(self, rid: int) -> np.ndarray:
+        n = ctypes.c_size_t()
+        lib().wl_server_result(self._s, rid, None, 0, ctypes.byref(n))
+        out = np.empty(n.value, dtype=np.float64)
+        _check(lib().wl_server_result(self._s, rid, _p(out), out.size, None), "wl_server_result")
+        return out
+
+    def release(self, rid: int):
+        _check(lib().wl_server_release(self._s, rid), "wl_server_release")
+
+    def close(self):
+        if self._s:
+            lib().wl_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

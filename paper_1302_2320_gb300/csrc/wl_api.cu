@@ -23,8 +23,10 @@
 
 #include "../../include/wl.h"
 #include "wl_kernels.cuh"
+#include "wl_runtime.cuh"
 
 using namespace wl;
+using namespace wl::rt;
 
 namespace {
 
@@ -49,10 +51,6 @@ wl_status fail(wl_status s, const char* fmt, ...)
                         __FILE__, __LINE__);                                              \
     } while (0)
 
-struct LatInfo {
-    int type, L, N, NB, z;
-};
-
 bool lattice_info(int type, int L, LatInfo* o)
 {
     if (L < 3) return false;
@@ -68,33 +66,29 @@ bool lattice_info(int type, int L, LatInfo* o)
         if (L > 101) return false;
         o->N = L * L * L;
         o->z = 6;
+    } else if (type == WL_SQUARE_OPEN) {
+        o->N = L * L;
+        o->z = 4;
     } else {
         return false;
     }
     if (o->N > (1 << 20)) return false;
-    o->NB = o->N * o->z / 2;
+    o->NB = type == WL_SQUARE_OPEN ? 2 * L * (L - 1) : o->N * o->z / 2;
+    o->kstep = type == WL_SQUARE_OPEN ? 1 : 2;
     return true;
 }
 
-// Bins of line l: even k in [0, min(z*min(l, N-l), N_B)] (no more than z
-// unhappy bonds per minority spin).
+// Bins of line l: k in [0, min(z*min(l, N-l), N_B)] (no more than z unhappy
+// bonds per minority spin) with the lattice's spacing: every even k on the
+// periodic lattices (even degrees), every k with open boundaries.
 int line_nbins(const LatInfo& g, int ell)
 {
     const int lm = std::min(ell, g.N - ell);
     const int64_t khi = std::min<int64_t>((int64_t)g.z * lm, g.NB);
-    return (int)(khi / 2 + 1);
+    return (int)(khi / g.kstep + 1);
 }
 
 size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
-
-struct Layout {
-    int nlines;
-    int pstride;     // list entries per line
-    int W;           // spin words per line (multiple of 4)
-    bool idx16;
-    int64_t nbins_total;
-    std::vector<LineDesc> desc;
-};
 
 Layout make_layout(const LatInfo& g)
 {
@@ -123,7 +117,7 @@ size_t required_bytes(const LatInfo& g, const Layout& lo)
     b += (size_t)lo.nlines * sizeof(LineDesc) + (size_t)lo.nlines * sizeof(LineState);
     b += (size_t)lo.nlines * lo.pstride * isz;
     b += (size_t)lo.nlines * lo.W * 4;
-    b += (size_t)lo.nbins_total * (8 + 4 + 8);   // lng, hist, assembled output
+    b += (size_t)lo.nbins_total * (8 + 8 + 8);   // lng, hist, assembled output
     b += (size_t)lo.nlines * 3 * 4;               // queue, per-line queue heads, identity
     b += kTableN * (4 + 8) + 4096;
     return b;
@@ -165,64 +159,6 @@ namespace wl {
 // Lets other translation units of the library report through wl_last_error().
 void set_last_error(const char* msg) { g_err = msg; }
 }  // namespace wl
-
-struct wl_ctx {
-    LatInfo g{};
-    Layout lo;
-    // options
-    uint32_t seed = 1;
-    int det = 1;
-    int64_t C = 1000;
-    int64_t budget = (int64_t)1 << 62;
-    int mapping = 0;
-    int form = 0;
-    cudaStream_t user_stream = nullptr;
-    bool has_user_stream = false;
-    int64_t slice_moves = (int64_t)1 << 20;
-    int64_t timeout_ms = 0;
-    int64_t hbm_budget = 0;
-    int ell_min = 0, ell_max = 0;
-    // state
-    bool allocated = false, initialized = false, assembled = false;
-    double u = 0.0;
-    int flat_pm = 0;
-    int q = 0;
-    int last_mapping = 0;
-    int64_t launches = 0;
-    double walk_ms = 0, init_ms = 0, assemble_ms = 0;
-    int64_t init_moves = 0;
-    // device
-    int device = 0, num_sms = 0;
-    size_t max_smem = 0;
-    cudaStream_t s = nullptr;
-    std::vector<cudaStream_t> pool;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_join = nullptr;
-    LineDesc* d_desc = nullptr;
-    LineState* d_st = nullptr;
-    void* d_perm = nullptr;
-    uint32_t* d_spins = nullptr;
-    int64_t* d_lng = nullptr;
-    uint32_t* d_hist = nullptr;
-    double* d_out = nullptr;
-    uint32_t* d_table = nullptr;
-    uint64_t* d_table64 = nullptr;
-    int32_t* d_order = nullptr;
-    int32_t* d_ident = nullptr;
-    int32_t* d_qheads = nullptr;
-    int32_t* d_flags = nullptr;
-    uint64_t* d_deadline = nullptr;
-    Summary* d_summary = nullptr;
-    Summary* h_summary = nullptr;         // pinned
-    int32_t* h_abort = nullptr;           // pinned, mapped
-    int32_t* d_abort = nullptr;
-    std::vector<uint64_t> table64;        // device-built table, copied back
-    int nqueue = 0;
-    // captured slice graph
-    cudaGraphExec_t graph = nullptr;
-    int graph_S = -1, graph_stage = -1;
-    unsigned graph_grid = 0, graph_block = 0;
-    WalkArgs graph_args{};          // arguments baked into the captured graph
-};
 
 namespace {
 
@@ -271,7 +207,7 @@ wl_status allocate(wl_ctx* h)
     if (!e) e = alloc(&h->d_perm, (size_t)lo.nlines * lo.pstride * isz);
     if (!e) e = alloc((void**)&h->d_spins, (size_t)lo.nlines * lo.W * 4);
     if (!e) e = alloc((void**)&h->d_lng, (size_t)lo.nbins_total * 8);
-    if (!e) e = alloc((void**)&h->d_hist, (size_t)lo.nbins_total * 4);
+    if (!e) e = alloc((void**)&h->d_hist, (size_t)lo.nbins_total * sizeof(hist_t));
     if (!e) e = alloc((void**)&h->d_out, (size_t)lo.nbins_total * 8);
     if (!e) e = alloc((void**)&h->d_table, kTableN * 4);
     if (!e) e = alloc((void**)&h->d_table64, kTableN * 8);
@@ -369,7 +305,7 @@ wl_status initialise(wl_ctx* h, double u, int flat_pm)
     a.seed = h->seed;
     a.F0 = std::llround(1.0 / u);
     CU(cudaEventRecord(h->ev0, h->s));
-    CU(launch_init(h->g.type, h->lo.idx16, a, h->s));
+    CU(launch_init(h->g.type == WL_SQUARE_OPEN ? (int)kSquareOpen : h->g.type, h->lo.idx16, a, h->s));
     CU(cudaEventRecord(h->ev1, h->s));
     if (h->ell_min > 0 || h->ell_max < h->lo.nlines - 1) {
         std::vector<LineState> out(h->lo.nlines);
@@ -415,6 +351,7 @@ WalkArgs base_args(wl_ctx* h)
     a.seed = h->seed;
     a.flat_pm = h->flat_pm;
     a.pstride = h->lo.pstride;
+    a.same_f_resets = h->same_f_resets;
     a.C = h->C;
     a.budget = h->budget;
     a.slice_moves = h->slice_moves;
@@ -425,15 +362,6 @@ WalkArgs base_args(wl_ctx* h)
 }
 
 int kernel_lattice(const wl_ctx* h);
-
-// Launch shape of the persistent form for S lanes per walker: stage lists and
-// spins in shared memory when at least one warp of walkers fits.
-struct Shape {
-    dim3 grid, block;
-    size_t smem;
-    int stage;
-    int slot;
-};
 
 wl_status persistent_shape(wl_ctx* h, int S, int* blocks_per_sm_out, Shape* sh)
 {
@@ -544,7 +472,7 @@ wl_status run_slice(wl_ctx* h, int S, const Shape& sh, bool use_graph)
 wl_status check_flags(wl_ctx* h, const Summary& sm)
 {
     if (sm.flags & 8) return fail(WL_ECUDA, "walker state invariant broken (k' outside its bins)");
-    if (sm.overflow || (sm.flags & 4)) return fail(WL_EOVERFLOW, "a histogram bin exceeded 2^31-1 within one stage");
+    if (sm.overflow || (sm.flags & 4)) return fail(WL_EOVERFLOW, "a histogram bin exceeded 2^63-1 within one stage");
     if (sm.flags & 3) {
         CU(cudaMemsetAsync(h->d_flags, 0, 16, h->s));
         *h->h_abort = 0;
@@ -559,12 +487,15 @@ wl_status check_flags(wl_ctx* h, const Summary& sm)
 int kernel_lattice(const wl_ctx* h)
 {
     if (h->g.type == WL_SQUARE && (h->g.L & (h->g.L - 1)) == 0) return kSquareP2;
+    if (h->g.type == WL_SQUARE_OPEN) return kSquareOpen;
     return h->g.type;
 }
 
-int pick_mapping_default(const wl_ctx* h)
+// 32 lanes per walker: on the 64x64 lattice the acceptance scan commits ~20
+// moves per batch and this mapping was fastest for every lattice measured.
+int pick_mapping_default(const wl_ctx*)
 {
-    return h->g.N <= 8192 ? 8 : 1;
+    return 32;
 }
 
 // Persistent form: slices until every selected line converged or hit the
@@ -712,6 +643,55 @@ bool valid_handle(wl_handle h) { return h != nullptr; }
 
 }  // namespace
 
+namespace wl {
+namespace rt {
+
+wl_status prepare(wl_ctx* h, double ln_f_min, double flatness, cudaStream_t after)
+{
+    if (!(ln_f_min >= 1e-10 && ln_f_min <= 0.5)) return fail(WL_EINVAL, "ln_f_min must be in [1e-10, 0.5]");
+    if (!(flatness > 0.0 && flatness <= 1.0)) return fail(WL_EINVAL, "flatness must be in (0, 1]");
+    if (h->ell_min > h->ell_max) return fail(WL_EINVAL, "ell_min > ell_max");
+    const int flat_pm = (int)std::lround(flatness * 1000.0);
+    if (flat_pm < 1) return fail(WL_EINVAL, "flatness below 0.001");
+    wl_status st = allocate(h);
+    if (st) return st;
+    if (after) {
+        CU(cudaEventRecord(h->ev_join, after));
+        CU(cudaStreamWaitEvent(h->s, h->ev_join, 0));
+    }
+    if (!h->initialized) {
+        st = initialise(h, ln_f_min, flat_pm);
+        if (st) return st;
+        h->launches += 2;
+    } else if (ln_f_min != h->u || flat_pm != h->flat_pm) {
+        return fail(WL_EINVAL, "a continued run must use the same ln_f_min and flatness");
+    }
+    h->assembled = false;
+    return WL_OK;
+}
+
+wl_status choose_shape(wl_ctx* h, int* S, Shape* sh)
+{
+    int m = h->mapping;
+    if (m == 0) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find({h->g.type, h->g.L, h->det});
+        m = it != g_tune_cache.end() ? it->second : pick_mapping_default(h);
+    }
+    *S = m;
+    h->last_mapping = m;
+    return persistent_shape(h, m, nullptr, sh);
+}
+
+wl_status launch_slice_async(wl_ctx* h, int S, const Shape& sh) { return run_slice(h, S, sh, true); }
+
+wl_status summary_status(wl_ctx* h, const Summary& sm) { return check_flags(h, sm); }
+
+size_t handle_bytes(const wl_ctx* h) { return required_bytes(h->g, h->lo); }
+
+}  // namespace rt
+}  // namespace wl
+
 extern "C" {
 
 const char* wl_last_error(void) { return g_err.c_str(); }
@@ -755,7 +735,7 @@ wl_status wl_set_option(wl_handle h, const char* key, int64_t v)
     if (!valid_handle(h) || !key) return fail(WL_EINVAL, "NULL handle or key");
     const std::string k(key);
     const bool semantic = (k == "seed" || k == "deterministic" || k == "check_interval" ||
-                           k == "ell_min" || k == "ell_max");
+                           k == "ell_min" || k == "ell_max" || k == "same_f_resets");
     if (semantic && h->initialized)
         return fail(WL_ESTATE, "option '%s' changes the walk; call wl_reset first", key);
     if (k == "seed") {
@@ -788,6 +768,9 @@ wl_status wl_set_option(wl_handle h, const char* key, int64_t v)
     } else if (k == "hbm_budget") {
         if (v < 0) return fail(WL_EINVAL, "hbm_budget must be >= 0");
         h->hbm_budget = v;
+    } else if (k == "same_f_resets") {
+        if (v < 0 || v > 1000000) return fail(WL_EINVAL, "same_f_resets must be in [0, 10^6]");
+        h->same_f_resets = (int)v;
     } else if (k == "ell_min" || k == "ell_max") {
         if (v < 0 || v >= h->lo.nlines) return fail(WL_EINVAL, "%s must be in [0, %d]", key, h->lo.nlines - 1);
         (k == "ell_min" ? h->ell_min : h->ell_max) = (int)v;
@@ -812,10 +795,12 @@ wl_status wl_get_option(wl_handle h, const char* key, int64_t* v)
     else if (k == "timeout_ms") *v = h->timeout_ms;
     else if (k == "hbm_budget") *v = h->hbm_budget;
     else if (k == "ell_min") *v = h->ell_min;
+    else if (k == "same_f_resets") *v = h->same_f_resets;
     else if (k == "ell_max") *v = h->ell_max;
     else if (k == "N") *v = h->g.N;
     else if (k == "NB") *v = h->g.NB;
     else if (k == "z") *v = h->g.z;
+    else if (k == "k_step") *v = h->g.kstep;
     else if (k == "lines") *v = h->lo.nlines;
     else if (k == "bins") *v = h->lo.nbins_total;
     else if (k == "device_bytes") *v = (int64_t)required_bytes(h->g, h->lo);
@@ -842,27 +827,10 @@ wl_status wl_abort(wl_handle h)
 wl_status wl_run(wl_handle h, double ln_f_min, double flatness)
 {
     if (!valid_handle(h)) return fail(WL_EINVAL, "NULL handle");
-    if (!(ln_f_min >= 1e-10 && ln_f_min <= 0.5)) return fail(WL_EINVAL, "ln_f_min must be in [1e-10, 0.5]");
-    if (!(flatness > 0.0 && flatness <= 1.0)) return fail(WL_EINVAL, "flatness must be in (0, 1]");
-    if (h->ell_min > h->ell_max) return fail(WL_EINVAL, "ell_min > ell_max");
-    const int flat_pm = (int)std::lround(flatness * 1000.0);
-    if (flat_pm < 1) return fail(WL_EINVAL, "flatness below 0.001");
-    wl_status st = allocate(h);
-    if (st) return st;
     const auto t_start = std::chrono::steady_clock::now();
-    if (h->has_user_stream) {
-        CU(cudaEventRecord(h->ev_join, h->user_stream));
-        CU(cudaStreamWaitEvent(h->s, h->ev_join, 0));
-    }
     h->launches = 0;
-    if (!h->initialized) {
-        st = initialise(h, ln_f_min, flat_pm);
-        if (st) return st;
-        h->launches += 2;
-    } else if (ln_f_min != h->u || flat_pm != h->flat_pm) {
-        return fail(WL_EINVAL, "a continued run must use the same ln_f_min and flatness");
-    }
-    h->assembled = false;
+    wl_status st = wl::rt::prepare(h, ln_f_min, flatness, h->has_user_stream ? h->user_stream : nullptr);
+    if (st) return st;
     CU(launch_set_deadline(h->d_deadline, (uint64_t)h->timeout_ms * 1000000ull, h->s));
     CU(cudaEventRecord(h->ev0, h->s));
     st = h->form == 0 ? run_persistent(h, t_start) : run_plain(h);
@@ -921,7 +889,7 @@ wl_status wl_get_lng(wl_handle h, int ell, double* out, size_t cap, int* k_lo, i
     const LineDesc& d = h->lo.desc[li];
     if (n_out) *n_out = (size_t)d.nbins;
     if (k_lo) *k_lo = 0;
-    if (k_step) *k_step = 2;
+    if (k_step) *k_step = h->g.kstep;
     if (!out || cap < (size_t)d.nbins) return fail(WL_EINVAL, "output capacity %zu < %d bins", cap, d.nbins);
     CU(cudaMemcpyAsync(out, h->d_out + d.bin_off, (size_t)d.nbins * 8, cudaMemcpyDeviceToHost, h->s));
     CU(cudaStreamSynchronize(h->s));
@@ -1014,14 +982,38 @@ wl_status wl_get_line_state(wl_handle h, int ell, int64_t* scal, int32_t* perm, 
         CU(cudaStreamSynchronize(h->s));
     }
     if (hist || visited) {
-        std::vector<uint32_t> hw(d.nbins);
-        CU(cudaMemcpyAsync(hw.data(), h->d_hist + d.bin_off, (size_t)d.nbins * 4, cudaMemcpyDeviceToHost, h->s));
+        std::vector<hist_t> hw(d.nbins);
+        CU(cudaMemcpyAsync(hw.data(), h->d_hist + d.bin_off, (size_t)d.nbins * sizeof(hist_t),
+                           cudaMemcpyDeviceToHost, h->s));
         CU(cudaStreamSynchronize(h->s));
         for (int b = 0; b < d.nbins; ++b) {
             if (hist) hist[b] = (int64_t)(hw[b] & ~kVisited);
             if (visited) visited[b] = (hw[b] & kVisited) ? 1 : 0;
         }
     }
+    return WL_OK;
+}
+
+wl_status wl_thermo(wl_handle h, const double* T, int nT, const double* H, int nH, double* out)
+{
+    if (!valid_handle(h) || !T || !H || !out || nT < 1 || nH < 1) return fail(WL_EINVAL, "bad arguments");
+    if (!h->assembled) return fail(WL_ESTATE, "call wl_assemble first");
+    if (h->ell_min != 0 || h->ell_max != h->lo.nlines - 1)
+        return fail(WL_ESTATE, "thermodynamics needs every line l = 0..N/2");
+    for (int a = 0; a < nT; ++a)
+        if (!(T[a] > 0.0)) return fail(WL_EINVAL, "temperatures must be > 0");
+    const size_t nd = (size_t)nT + (size_t)nH + 6 * (size_t)nT * (size_t)nH;
+    double* d = nullptr;
+    CU(cudaMallocAsync(&d, nd * sizeof(double), h->s));
+    cudaError_t e = cudaMemcpyAsync(d, T, nT * sizeof(double), cudaMemcpyHostToDevice, h->s);
+    if (!e) e = cudaMemcpyAsync(d + nT, H, nH * sizeof(double), cudaMemcpyHostToDevice, h->s);
+    if (!e) e = launch_thermo(h->d_desc, h->lo.nlines, h->d_out, h->g.N, h->g.NB, h->g.kstep, d, nT,
+                              d + nT, nH, d + nT + nH, h->s);
+    if (!e) e = cudaMemcpyAsync(out, d + nT + nH, 6 * (size_t)nT * nH * sizeof(double),
+                                cudaMemcpyDeviceToHost, h->s);
+    cudaFreeAsync(d, h->s);
+    if (!e) e = cudaStreamSynchronize(h->s);
+    if (e) return fail(WL_ECUDA, "wl_thermo: %s", cudaGetErrorString(e));
     return WL_OK;
 }
 

@@ -9,17 +9,20 @@
 
 namespace wl {
 
-constexpr uint32_t kVisited = 0x80000000u;   // hist word: bit 31 = bin ever visited
+using hist_t = uint64_t;                       // histogram word: count, bit 63 = ever visited
+constexpr hist_t kVisited = 1ull << 63;
 constexpr int kTableN = 4096;
 constexpr int kTableBytes = kTableN * 4;     // entries 1..4095 as u32; entry 0 is 2^32
 
 // kSquareP2: the square lattice when L is a power of two (coordinates by
 // shift and mask); the same lattice and bond set as kSquare.
-enum LatticeType : int { kSquare = 0, kTriangular = 1, kCubic = 2, kSquareP2 = 3 };
+// kSquareOpen: the square lattice with open boundaries (sites on an edge have
+// fewer neighbours; k takes every value, so bins have step 1).
+enum LatticeType : int { kSquare = 0, kTriangular = 1, kCubic = 2, kSquareP2 = 3, kSquareOpen = 4 };
 
-// Per-walker window of ln g (int64) and histogram (u32) bins in shared memory.
+// Per-walker window of ln g (int64) and histogram (u64) bins in shared memory.
 constexpr int kWin = 64;
-constexpr int kWinBytes = kWin * 12;
+constexpr int kWinBytes = kWin * 16;
 
 // Per-line scalar state (device, one per walked line).
 struct LineState {
@@ -55,7 +58,7 @@ struct WalkArgs {
     void* perm;              // lines x pstride list entries (uint16 if N <= 65536, else uint32)
     uint32_t* spins;         // lines x W packed spins
     int64_t* lng;            // ragged ln g / u
-    uint32_t* hist;          // ragged histogram | kVisited
+    hist_t* hist;            // ragged histogram | kVisited
     const uint32_t* table;   // exp threshold table (kTableN words)
     const int32_t* order;    // work queue: line indices, most expensive first
     int32_t* qnext;          // work queue head
@@ -67,6 +70,7 @@ struct WalkArgs {
     int32_t stage_smem;      // 1: lists and spins staged in shared memory
     int32_t slot_bytes;      // shared bytes per walker slot (window + staged list/spins)
     int32_t pstride;         // list entries per line, N rounded up to 16 bytes
+    int32_t same_f_resets;   // R > 0: extra histogram resets at unchanged f (see walk_line)
     int64_t C;               // flatness check interval
     int64_t budget;          // per-line cap on t
     int64_t slice_moves;     // moves per line in this launch
@@ -147,8 +151,24 @@ __device__ __forceinline__ void neighbours(const Geo& g, uint32_t i, uint32_t* n
 }
 
 template <int LAT> struct Coord {
-    static constexpr int z = (LAT == kSquare || LAT == kSquareP2) ? 4 : 6;
+    static constexpr int z = (LAT == kSquare || LAT == kSquareP2 || LAT == kSquareOpen) ? 4 : 6;
+    static constexpr int kshift = LAT == kSquareOpen ? 0 : 1;   // bin of k = k >> kshift
+    static constexpr int zbin = (2 * z) >> kshift;                // largest bin step of a move
 };
+
+// Open boundaries: the neighbours that exist get their index, the others the
+// site itself with a cleared valid bit.
+__device__ __forceinline__ unsigned open_neighbours(const Geo& g, uint32_t i, uint32_t* nb)
+{
+    const uint32_t L = (uint32_t)g.L;
+    const uint32_t y = divL(g, i), x = i - y * L;
+    const unsigned v = (x + 1 < L ? 1u : 0u) | (x > 0 ? 2u : 0u) | (y + 1 < L ? 4u : 0u) | (y > 0 ? 8u : 0u);
+    nb[0] = (v & 1u) ? i + 1 : i;
+    nb[1] = (v & 2u) ? i - 1 : i;
+    nb[2] = (v & 4u) ? i + L : i;
+    nb[3] = (v & 8u) ? i - L : i;
+    return v;
+}
 
 // Change of k when up-spin i and down-spin j are exchanged.  With u_i, u_j the
 // up neighbours of i and j in the current configuration and a_ij the number
@@ -180,6 +200,20 @@ __device__ __forceinline__ int delta_k_nb(const Geo& g, const uint32_t* sp, uint
                                           uint32_t* ni, uint32_t* nj)
 {
     constexpr int z = Coord<LAT>::z;
+    if constexpr (LAT == kSquareOpen) {
+        // with degrees z_i, z_j: dk = 2 (u_i - u_j + a_ij) - z_i + z_j
+        const unsigned vi = open_neighbours(g, i, ni), vj = open_neighbours(g, j, nj);
+        int ui = 0, uj = 0, a = 0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            ui += (int)(((vi >> m) & 1u) & spin_at(sp, ni[m]));
+            uj += (int)(((vj >> m) & 1u) & spin_at(sp, nj[m]));
+            a += (int)(((vi >> m) & 1u) && ni[m] == j);
+            if (!((vi >> m) & 1u)) ni[m] = 0xFFFFFFFFu;     // never equal to a site
+            if (!((vj >> m) & 1u)) nj[m] = 0xFFFFFFFFu;
+        }
+        return 2 * (ui - uj + a) - __popc(vi) + __popc(vj);
+    }
     neighbours<LAT>(g, i, ni);
     neighbours<LAT>(g, j, nj);
     int ui = 0, uj = 0, a = 0;

@@ -27,12 +27,12 @@ __global__ void init_kernel(const InitArgs A)
     IDX* perm = reinterpret_cast<IDX*>(A.perm) + (size_t)li * A.pstride;
     uint32_t* sp = A.spins + (size_t)li * W;
     int64_t* lng = A.lng + D.bin_off;
-    uint32_t* hist = A.hist + D.bin_off;
+    hist_t* hist = A.hist + D.bin_off;
     for (int n = lane; n < A.pstride; n += 32) perm[n] = (IDX)(n < N ? n : 0);
     for (int w = lane; w < W; w += 32) sp[w] = 0u;
     for (int b = lane; b < D.nbins; b += 32) {
         lng[b] = 0;
-        hist[b] = 0u;
+        hist[b] = 0ull;
     }
     __syncwarp();
     const uint2 key = make_uint2((uint32_t)ell, A.seed);
@@ -64,10 +64,12 @@ __global__ void init_kernel(const InitArgs A)
     constexpr int z = Coord<LAT>::z;
     for (int n = lane; n < N; n += 32) {
         uint32_t nb[z];
-        neighbours<LAT>(A.g, (uint32_t)n, nb);
+        unsigned valid = (1u << z) - 1u;
+        if constexpr (LAT == kSquareOpen) valid = open_neighbours(A.g, (uint32_t)n, nb);
+        else neighbours<LAT>(A.g, (uint32_t)n, nb);
         const uint32_t sn = spin_at(sp, (uint32_t)n);
 #pragma unroll
-        for (int m = 0; m < z; ++m) twice += (int)(sn != spin_at(sp, nb[m]));
+        for (int m = 0; m < z; ++m) twice += (int)(((valid >> m) & 1u) && sn != spin_at(sp, nb[m]));
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) twice += __shfl_xor_sync(0xffffffffu, twice, off);
@@ -83,7 +85,7 @@ __global__ void init_kernel(const InitArgs A)
         s.checks = 0;
         s.batches = 0;
         if (ell == 0) {
-            hist[s.k >> 1] = kVisited;
+            hist[s.k >> Coord<LAT>::kshift] = kVisited;
             s.F = 0;
             s.status = 1;
         }
@@ -93,6 +95,7 @@ __global__ void init_kernel(const InitArgs A)
 
 cudaError_t launch_init(int lattice, bool idx16, const InitArgs& a, cudaStream_t s)
 {
+    clear_stale_error();
     const int warps = 4;
     const dim3 grid((a.nlines + warps - 1) / warps), block(32 * warps);
     if (lattice == kSquare) {
@@ -101,9 +104,12 @@ cudaError_t launch_init(int lattice, bool idx16, const InitArgs& a, cudaStream_t
     } else if (lattice == kTriangular) {
         if (idx16) init_kernel<kTriangular, uint16_t><<<grid, block, 0, s>>>(a);
         else init_kernel<kTriangular, uint32_t><<<grid, block, 0, s>>>(a);
-    } else {
+    } else if (lattice == kCubic) {
         if (idx16) init_kernel<kCubic, uint16_t><<<grid, block, 0, s>>>(a);
         else init_kernel<kCubic, uint32_t><<<grid, block, 0, s>>>(a);
+    } else {
+        if (idx16) init_kernel<kSquareOpen, uint16_t><<<grid, block, 0, s>>>(a);
+        else init_kernel<kSquareOpen, uint32_t><<<grid, block, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
@@ -113,7 +119,7 @@ cudaError_t launch_init(int lattice, bool idx16, const InitArgs& a, cudaStream_t
 //   ln g_kl = ln C(N,l) + u lng[b] - (M + ln sum_visited exp(u lng[b] - M)),
 // M the visited maximum; unvisited bins get -inf.  FP64.
 // ---------------------------------------------------------------------------
-__global__ void assemble_kernel(const LineDesc* desc, const int64_t* lng, const uint32_t* hist,
+__global__ void assemble_kernel(const LineDesc* desc, const int64_t* lng, const hist_t* hist,
                                 int N, int nlines, double u, double* out)
 {
     const int warps = blockDim.x >> 5;
@@ -122,7 +128,7 @@ __global__ void assemble_kernel(const LineDesc* desc, const int64_t* lng, const 
     if (li >= nlines) return;
     const LineDesc D = desc[li];
     const int64_t* lg = lng + D.bin_off;
-    const uint32_t* h = hist + D.bin_off;
+    const hist_t* h = hist + D.bin_off;
     double* o = out + D.bin_off;
     double mx = -DBL_MAX;
     for (int b = lane; b < D.nbins; b += 32)
@@ -141,9 +147,10 @@ __global__ void assemble_kernel(const LineDesc* desc, const int64_t* lng, const 
         o[b] = (h[b] & kVisited) ? lnC + u * (double)lg[b] - lse : -INFINITY;
 }
 
-cudaError_t launch_assemble(const LineDesc* desc, const int64_t* lng, const uint32_t* hist, int N,
+cudaError_t launch_assemble(const LineDesc* desc, const int64_t* lng, const hist_t* hist, int N,
                             int nlines, double u, double* out, cudaStream_t s)
 {
+    clear_stale_error();
     const int warps = 8;
     assemble_kernel<<<(nlines + warps - 1) / warps, 32 * warps, 0, s>>>(desc, lng, hist, N, nlines,
                                                                        u, out);
@@ -244,6 +251,7 @@ __global__ void exp_table_kernel(double u, int q, uint64_t* out)
 
 cudaError_t launch_exp_table(double u, int q, uint64_t* out, cudaStream_t s)
 {
+    clear_stale_error();
     exp_table_kernel<<<(kTableN + 255) / 256, 256, 0, s>>>(u, q, out);
     return cudaGetLastError();
 }
@@ -268,6 +276,7 @@ cudaError_t launch_philox(size_t n, const uint32_t* ctr, const uint32_t* key, ui
                           cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
+    clear_stale_error();
     philox_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, ctr, key, out);
     return cudaGetLastError();
 }
@@ -339,7 +348,118 @@ __global__ void summary_kernel(const LineState* st, int nlines, int64_t budget,
 cudaError_t launch_summary(const LineState* st, int nlines, int64_t budget, const int32_t* flags,
                            Summary* out, cudaStream_t s)
 {
+    clear_stale_error();
     summary_kernel<<<1, 1024, 0, s>>>(st, nlines, budget, flags, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Thermodynamics from the assembled surface (Eq. 2 with the energy of Eq. 1):
+// one block per (T, H) point, Z = sum_{k,l} g_kl exp(-E_kl / T),
+// E_kl = -(N_B - 2k) - H M, M = 2l - N; line l > N/2 is line N - l.  A single
+// pass keeps an online log-sum-exp (running maximum, sums rescaled when it
+// grows) of the weights and of the weighted E, E^2, M, |M|, M^2; FP64.
+// ---------------------------------------------------------------------------
+struct ThermoAcc {
+    double mx, z, e1, e2, m1, ma, m2;
+};
+
+__device__ __forceinline__ void thermo_add(ThermoAcc& a, double x, double E, double M)
+{
+    if (x > a.mx) {
+        const double r = exp(a.mx - x);
+        a.z *= r; a.e1 *= r; a.e2 *= r; a.m1 *= r; a.ma *= r; a.m2 *= r;
+        a.mx = x;
+    }
+    const double w = exp(x - a.mx);
+    a.z += w;
+    a.e1 += w * E;
+    a.e2 += w * E * E;
+    a.m1 += w * M;
+    a.ma += w * fabs(M);
+    a.m2 += w * M * M;
+}
+
+__device__ __forceinline__ void thermo_merge(ThermoAcc& a, const ThermoAcc& b)
+{
+    if (b.mx == -INFINITY) return;
+    if (a.mx == -INFINITY) {
+        a = b;
+        return;
+    }
+    const double m = fmax(a.mx, b.mx), ra = exp(a.mx - m), rb = exp(b.mx - m);
+    a.z = a.z * ra + b.z * rb;
+    a.e1 = a.e1 * ra + b.e1 * rb;
+    a.e2 = a.e2 * ra + b.e2 * rb;
+    a.m1 = a.m1 * ra + b.m1 * rb;
+    a.ma = a.ma * ra + b.ma * rb;
+    a.m2 = a.m2 * ra + b.m2 * rb;
+    a.mx = m;
+}
+
+__device__ __forceinline__ ThermoAcc shfl_acc(const ThermoAcc& a, int off)
+{
+    ThermoAcc b;
+    b.mx = __shfl_xor_sync(0xffffffffu, a.mx, off);
+    b.z = __shfl_xor_sync(0xffffffffu, a.z, off);
+    b.e1 = __shfl_xor_sync(0xffffffffu, a.e1, off);
+    b.e2 = __shfl_xor_sync(0xffffffffu, a.e2, off);
+    b.m1 = __shfl_xor_sync(0xffffffffu, a.m1, off);
+    b.ma = __shfl_xor_sync(0xffffffffu, a.ma, off);
+    b.m2 = __shfl_xor_sync(0xffffffffu, a.m2, off);
+    return b;
+}
+
+__global__ void thermo_kernel(const LineDesc* desc, int nlines, const double* lng, int N, int NB,
+                              int kstep, const double* T, const double* H, int nH, double* out)
+{
+    const int pt = blockIdx.x;
+    const double beta = 1.0 / T[pt / nH], h = H[pt % nH];
+    ThermoAcc acc = {-INFINITY, 0, 0, 0, 0, 0, 0};
+    for (int li = 0; li < nlines; ++li) {
+        const LineDesc D = desc[li];
+        const int l = D.ell, lm = N - D.ell;
+        const double Mp = (double)(2 * l - N), Mm = (double)(2 * lm - N);
+        for (int b = threadIdx.x; b < D.nbins; b += blockDim.x) {
+            const double g = lng[D.bin_off + b];
+            if (isinf(g)) continue;
+            const double bond = -(double)(NB - 2 * kstep * b);       // k = kstep * b
+            const double Ep = bond - h * Mp;
+            thermo_add(acc, g - beta * Ep, Ep, Mp);
+            if (lm != l) {
+                const double Em = bond - h * Mm;
+                thermo_add(acc, g - beta * Em, Em, Mm);
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) thermo_merge(acc, shfl_acc(acc, off));
+    __shared__ ThermoAcc part[32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) part[w] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ThermoAcc a = part[0];
+        for (int x = 1; x < (int)(blockDim.x >> 5); ++x) thermo_merge(a, part[x]);
+        const double e1 = a.e1 / a.z, e2 = a.e2 / a.z, m1 = a.m1 / a.z, ma = a.ma / a.z,
+                     m2 = a.m2 / a.z;
+        double* o = out + (size_t)pt * 6;
+        o[0] = (a.mx + log(a.z)) / N;
+        o[1] = e1 / N;
+        o[2] = (e2 - e1 * e1) * beta * beta / N;
+        o[3] = m1 / N;
+        o[4] = ma / N;
+        o[5] = (m2 - m1 * m1) * beta / N;
+    }
+}
+
+cudaError_t launch_thermo(const LineDesc* desc, int nlines, const double* lng, int N, int NB,
+                          int kstep, const double* T, int nT, const double* H, int nH, double* out,
+                          cudaStream_t s)
+{
+    if (nT * nH == 0) return cudaSuccess;
+    clear_stale_error();
+    thermo_kernel<<<nT * nH, 256, 0, s>>>(desc, nlines, lng, N, NB, kstep, T, H, nH, out);
     return cudaGetLastError();
 }
 
@@ -350,6 +470,7 @@ __global__ void deadline_kernel(uint64_t* deadline, uint64_t timeout_ns)
 
 cudaError_t launch_set_deadline(uint64_t* deadline, uint64_t timeout_ns, cudaStream_t s)
 {
+    clear_stale_error();
     deadline_kernel<<<1, 1, 0, s>>>(deadline, timeout_ns);
     return cudaGetLastError();
 }
@@ -362,6 +483,8 @@ cudaError_t launch_walk(int lattice, int S, bool det, bool idx16, dim3 grid, dim
         return launch_walk_square_p2(S, det, idx16, grid, block, smem, s, a, nullptr);
     if (lattice == kTriangular)
         return launch_walk_triangular(S, det, idx16, grid, block, smem, s, a, nullptr);
+    if (lattice == kSquareOpen)
+        return launch_walk_square_open(S, det, idx16, grid, block, smem, s, a, nullptr);
     return launch_walk_cubic(S, det, idx16, grid, block, smem, s, a, nullptr);
 }
 
@@ -375,6 +498,8 @@ cudaError_t walk_kernel_attrs(int lattice, int S, bool det, bool idx16, size_t s
         return launch_walk_square_p2(S, det, idx16, z, b, smem, 0, dummy, blocks_per_sm);
     if (lattice == kTriangular)
         return launch_walk_triangular(S, det, idx16, z, b, smem, 0, dummy, blocks_per_sm);
+    if (lattice == kSquareOpen)
+        return launch_walk_square_open(S, det, idx16, z, b, smem, 0, dummy, blocks_per_sm);
     return launch_walk_cubic(S, det, idx16, z, b, smem, 0, dummy, blocks_per_sm);
 }
 

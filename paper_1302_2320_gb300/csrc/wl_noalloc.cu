@@ -97,7 +97,7 @@ extern "C" wl_status wl_walk_noalloc(wl_lattice lattice, int L, int ell_first, i
                                      uint32_t seed, int deterministic, double ln_f_min,
                                      double flatness, int64_t check_interval, int64_t move_budget,
                                      int mapping, int init, void* perm, uint32_t* spins,
-                                     int64_t* lng, uint32_t* hist, int64_t* state,
+                                     int64_t* lng, uint64_t* hist, int64_t* state,
                                      int64_t stream)
 {
     // ---- arguments (host only; nothing is launched on a rejected call) ----
@@ -124,8 +124,8 @@ extern "C" wl_status wl_walk_noalloc(wl_lattice lattice, int L, int ell_first, i
         return nfail(WL_EINVAL, "mapping must be 0, 1, 2, 4, 8, 16 or 32");
     if (!perm || !spins || !lng || !hist || !state) return nfail(WL_EINVAL, "NULL buffer");
     if (((uintptr_t)perm | (uintptr_t)spins) & 15u) return nfail(WL_EINVAL, "perm and spins must be 16-byte aligned");
-    if (((uintptr_t)lng | (uintptr_t)state) & 7u || ((uintptr_t)hist & 3u))
-        return nfail(WL_EINVAL, "lng/state must be 8-byte and hist 4-byte aligned");
+    if (((uintptr_t)lng | (uintptr_t)state | (uintptr_t)hist) & 7u)
+        return nfail(WL_EINVAL, "lng, hist and state must be 8-byte aligned");
     const int q = noalloc_q(ln_f_min);
     if (q < 0) return nfail(WL_EINVAL, "ln_f_min out of range");
     const cudaStream_t s = (cudaStream_t)(intptr_t)stream;

@@ -1,20 +1,26 @@
 // wl_walk.cuh -- the Wang-Landau walker kernel for micromagnetic lines
 // (arXiv:1302.2320, the procedure around Eq. 3 and Eq. 4).
 //
-// One walker = one line l = S consecutive lanes of a warp ("group").  The S
-// lanes evaluate the S consecutive steps t, t+1, ..., t+S-1 from the same
-// state: lane m draws Philox(ctr = t+m) and computes its proposal (U[a], D[b]),
-// k' and its accept decision.  The m earlier steps of the batch, if all
-// rejected, each added ln f at the current bin, so lane m tests against
-// ln g(k) + m ln f when k' != k (k' == k is always accepted).  The first
-// accepting lane m* commits m* rejections and its accept; the next batch starts
-// at t + m* + 1.  Because the random numbers are keyed by t, the committed
-// chain is the sequential chain, bit for bit, for every S.  Batches never
-// cross a flatness check (t multiple of C) or the end of the slice.
+// One walker = one line l = S consecutive lanes of a warp ("group").  A batch
+// covers the steps t .. t+S-1:
+//   parallel phase -- lane m draws Philox(ctr = t+m) and evaluates its
+//     exchange proposal against the state at the start of the batch: list
+//     slots a, b, sites i = U[a], j = D[b], their neighbours and the change of
+//     k (all of this is independent of the acceptance decisions);
+//   serial scan -- the group resolves the steps in order with Eq. 3 against the
+//     current k and ln g (every lane computes the same scan state).  An accepted
+//     exchange of (i_s, j_s) leaves a later proposal exact unless it reuses list
+//     slot a_s or b_s or has i_s or j_s among its sites' neighbours; such
+//     proposals are marked, and the batch ends at the first marked one (or
+//     when a proposal's bin leaves the group's ln g window).
+// The accepted exchanges of a batch are mutually independent and are applied
+// together after the scan.  Random numbers are keyed by t, so the committed
+// chain is the sequential chain, bit for bit, for every S.  Batches never cross
+// a flatness check (t multiple of C) or the end of the slice.
 //
 // The current bin's ln g and histogram are kept in registers (plus a pending
-// count) and written back when the walker leaves the bin or reaches a check;
-// every other bin is up to date in global memory.
+// count); the bins around it live in a shared-memory window that is written
+// back when the walker re-centres it, at every check and at the end.
 #pragma once
 
 #include "wl_device.cuh"
@@ -32,24 +38,27 @@ __device__ __forceinline__ unsigned group_mask(int gbase)
 // n visited bins, Ssum = their histogram total, c = bins with
 // 1000*n*h >= flat_pm*Ssum; flat iff 1000*c >= flat_pm*n.
 template <int S>
-__device__ bool group_flat(const uint32_t* hist, int nbins, int m, unsigned gmask, int flat_pm)
+__device__ bool group_flat(const hist_t* hist, int nbins, int m, unsigned gmask, int flat_pm)
 {
-    int64_t n = 0, ssum = 0;
+    int64_t n = 0;
+    uint64_t ssum = 0;
     for (int b = m; b < nbins; b += S) {
-        const uint32_t h = hist[b];
+        const hist_t h = hist[b];
         if (h & kVisited) {
             n += 1;
-            ssum += (int64_t)(h & ~kVisited);
+            ssum += h & ~kVisited;
         }
     }
     n = group_sum<S>(gmask, n);
     ssum = group_sum<S>(gmask, ssum);
     if (n == 0) return false;
     int64_t c = 0;
-    const int64_t rhs = (int64_t)flat_pm * ssum;
+    // products of up to ~2^77: compared in 128-bit integers
+    const unsigned __int128 rhs = (unsigned __int128)flat_pm * ssum;
+    const unsigned __int128 scale = (unsigned __int128)(1000 * n);
     for (int b = m; b < nbins; b += S) {
-        const uint32_t h = hist[b];
-        if ((h & kVisited) && 1000 * n * (int64_t)(h & ~kVisited) >= rhs) c += 1;
+        const hist_t h = hist[b];
+        if ((h & kVisited) && scale * (h & ~kVisited) >= rhs) c += 1;
     }
     c = group_sum<S>(gmask, c);
     return 1000 * c >= (int64_t)flat_pm * n;
@@ -59,14 +68,14 @@ __device__ bool group_flat(const uint32_t* hist, int nbins, int m, unsigned gmas
 // minimum of ln g at zero stands in for the normalisation of Eq. 4 (Eq. 4 is
 // applied exactly at assembly); the histogram is reset, visited bits kept.
 template <int S>
-__device__ void group_stage_step(int64_t* lng, uint32_t* hist, int nbins, int m, unsigned gmask)
+__device__ void group_stage_step(int64_t* lng, hist_t* hist, int nbins, int m, unsigned gmask)
 {
     int64_t mn = INT64_MAX;
     for (int b = m; b < nbins; b += S)
         if (hist[b] & kVisited) mn = lng[b] < mn ? lng[b] : mn;
     mn = group_min<S>(gmask, mn);
     for (int b = m; b < nbins; b += S) {
-        const uint32_t h = hist[b];
+        const hist_t h = hist[b];
         if (h & kVisited) lng[b] -= mn;
         hist[b] = h & kVisited;
     }
@@ -79,7 +88,7 @@ __device__ void group_stage_step(int64_t* lng, uint32_t* hist, int nbins, int m,
 // an edge that is not the line's own edge.
 
 template <int S>
-__device__ __forceinline__ void window_store(int64_t* wl, uint32_t* wh, int64_t* lng, uint32_t* hist,
+__device__ __forceinline__ void window_store(int64_t* wl, hist_t* wh, int64_t* lng, hist_t* hist,
                                              int wb, int wn, int m)
 {
     for (int x = m; x < wn; x += S) {
@@ -89,8 +98,8 @@ __device__ __forceinline__ void window_store(int64_t* wl, uint32_t* wh, int64_t*
 }
 
 template <int S>
-__device__ __forceinline__ void window_load(int64_t* wl, uint32_t* wh, const int64_t* lng,
-                                            const uint32_t* hist, int wb, int wn, int m)
+__device__ __forceinline__ void window_load(int64_t* wl, hist_t* wh, const int64_t* lng,
+                                            const hist_t* hist, int wb, int wn, int m)
 {
     for (int x = m; x < wn; x += S) {
         wl[x] = lng[wb + x];
@@ -112,7 +121,7 @@ __device__ __forceinline__ uint4 philox_step(uint64_t t, uint2 key)
 
 // Walk line `li` for up to A.slice_moves moves (or to its budget, or to
 // convergence).  perm/sp point at the line's list and spins (shared or global
-// memory); win is the group's window (kWin int64 ln g, then kWin u32 hist).
+// memory); win is the group's window (kWin int64 ln g, then kWin u64 hist).
 // All lanes of the group hold identical copies of the scalar state.  The
 // current bin's ln g, histogram word and pending count live in registers and
 // are authoritative; every other bin is up to date in the window (inside it)
@@ -127,7 +136,8 @@ template <int LAT, int S, bool DET, typename IDX>
 __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned gmask,
                           IDX* perm, uint32_t* sp, const uint32_t* tab, uint8_t* win)
 {
-    constexpr int zb = Coord<LAT>::z;     // largest bin step of one move
+    constexpr int zb = Coord<LAT>::zbin;  // largest bin step of one move
+    constexpr int ks = Coord<LAT>::kshift;
     const LineDesc D = A.desc[li];
     LineState* P = A.st + li;
     int64_t k = P->k, t = P->t, F = P->F, stage = P->stage, accepts = P->accepts;
@@ -137,20 +147,20 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
     const int ell = D.ell, nbins = D.nbins;
     const uint32_t nd = (uint32_t)(A.g.N - ell);
     int64_t* lng = A.lng + D.bin_off;
-    uint32_t* hist = A.hist + D.bin_off;
+    hist_t* hist = A.hist + D.bin_off;
     int64_t* wl = reinterpret_cast<int64_t*>(win);
-    uint32_t* wh = reinterpret_cast<uint32_t*>(win + kWin * 8);
+    hist_t* wh = reinterpret_cast<hist_t*>(win + kWin * 8);
     const uint2 key = make_uint2((uint32_t)ell, A.seed);
     int64_t end = t + A.slice_moves;
     if (end > A.budget) end = A.budget;
 
-    int bc = (int)(k >> 1);
+    int bc = (int)(k >> ks);
     int wb = window_base(bc, nbins);
     const int wn = nbins < kWin ? nbins : kWin;
     window_load<S>(wl, wh, lng, hist, wb, wn, m);
     __syncwarp(gmask);
     int64_t cur = wl[bc - wb];
-    uint32_t hcur = wh[bc - wb];
+    hist_t hcur = wh[bc - wb];
     uint32_t pend = 0;
     int stop = 0;
 
@@ -175,7 +185,8 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
             const uint32_t b = pick(r0.y, nd);
             const uint32_t i = (uint32_t)perm[a];
             const uint32_t j = (uint32_t)perm[ell + b];
-            uint32_t ni[zb], nj[zb];
+            constexpr int zc = Coord<LAT>::z;
+            uint32_t ni[zc], nj[zc];
             const int dk = delta_k_nb<LAT>(A.g, sp, i, j, ni, nj);
             if (needf) r1 = rf;
             // -- serial phase: the steps in order with Eq. 3 against the current
@@ -185,10 +196,16 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
             //    batch ends at the first marked one.
             unsigned inv = 0u, accm = 0u;
             int c = lim;
+            // step s's change of k and random word, shuffled one step ahead
+            int dkn = __shfl_sync(gmask, dk, gbase);
+            uint32_t rzn = __shfl_sync(gmask, r0.z, gbase);
             for (int s = 0; s < lim; ++s) {
                 const int src = gbase + s;
-                const int dks = __shfl_sync(gmask, dk, src);
-                const uint32_t rzs = __shfl_sync(gmask, r0.z, src);
+                const int dks = dkn;
+                const uint32_t rzs = rzn;
+                const int nxt = gbase + (s + 1 < S ? s + 1 : s);
+                dkn = __shfl_sync(gmask, dk, nxt);
+                rzn = __shfl_sync(gmask, r0.z, nxt);
                 if ((inv >> s) & 1u) {
                     c = s;
                     break;
@@ -197,7 +214,7 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
                 bool acc = true;
                 int64_t lp = 0;
                 if (dks != 0) {
-                    const int bp = kp >> 1;
+                    const int bp = kp >> ks;
                     const int wx = bp - wb;
                     if ((unsigned)bp >= (unsigned)nbins) {      // invariant broken
                         stop = 4;
@@ -220,12 +237,12 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
                 accm |= 1u << s;
                 if (dks != 0) {
                     // leave the current bin: its ln g and histogram go to the window
-                    if ((uint64_t)(hcur & ~kVisited) + pend >= (uint64_t)kVisited) stop = 2;
+                    if ((hcur & ~kVisited) + pend >= kVisited) stop = 2;
                     if (pend) hcur = (hcur + pend) | kVisited;
                     wl[bc - wb] = cur;
                     wh[bc - wb] = hcur;
                     k = kp;
-                    bc = kp >> 1;
+                    bc = kp >> ks;
                     cur = lp + F;
                     hcur = wh[bc - wb];
                     pend = 1u;
@@ -238,7 +255,7 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
                 const uint32_t is = __shfl_sync(gmask, i, src), js = __shfl_sync(gmask, j, src);
                 bool conf = (a == as) | (b == bs);
 #pragma unroll
-                for (int q = 0; q < zb; ++q)
+                for (int q = 0; q < zc; ++q)
                     conf |= (ni[q] == is) | (ni[q] == js) | (nj[q] == is) | (nj[q] == js);
                 unsigned cb = __ballot_sync(gmask, conf && m > s);
                 if constexpr (S < 32) cb = (cb >> gbase) & ((1u << S) - 1u);
@@ -289,7 +306,7 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
 
         if (t == next_check) {
             // current bin -> window -> global, then test flatness over the line
-            if ((uint64_t)(hcur & ~kVisited) + pend >= (uint64_t)kVisited) {
+            if ((hcur & ~kVisited) + pend >= kVisited) {
                 stop = 2;
                 break;
             }
@@ -303,7 +320,17 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
             window_store<S>(wl, wh, lng, hist, wb, wn, m);
             __syncwarp(gmask);
             checks += 1;
-            if (group_flat<S>(hist, nbins, m, gmask, A.flat_pm)) {
+            const bool flat = group_flat<S>(hist, nbins, m, gmask, A.flat_pm);
+            if (!flat && A.same_f_resets > 0 && (t - t_stage) / A.C <= A.same_f_resets) {
+                // extra reset at unchanged f within the first R checks of a
+                // stage (the remark after Eq. 4): histogram reset, ln g shifted
+                group_stage_step<S>(lng, hist, nbins, m, gmask);
+                window_load<S>(wl, wh, lng, hist, wb, wn, m);
+                __syncwarp(gmask);
+                cur = wl[bc - wb];
+                hcur = wh[bc - wb];
+            }
+            if (flat) {
                 group_stage_step<S>(lng, hist, nbins, m, gmask);
                 F >>= 2;                     // ln f -> ln f / 4
                 stage += 1;

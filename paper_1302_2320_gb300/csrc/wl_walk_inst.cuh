@@ -14,17 +14,26 @@ cudaError_t walk_one(dim3 grid, dim3 block, size_t smem, cudaStream_t s, const W
                      int* bps)
 {
     auto* fn = walk_kernel<LAT, S, DET, IDX>;
-    // the shared-memory attribute is set outside stream capture only
+    // The dynamic shared-memory limit is a property of the kernel function,
+    // shared by every handle: raise it to the device maximum (outside stream
+    // capture) and never lower it, so a captured launch of one handle stays
+    // valid whatever shape another handle uses.
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (!bps) {
         cudaError_t e = cudaStreamIsCapturing(s, &cap);
         if (e != cudaSuccess) return e;
     }
     if (cap == cudaStreamCaptureStatusNone) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int dev = 0, optin = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin > (int)smem ? optin : (int)smem);
         if (e != cudaSuccess) return e;
     }
     if (bps) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fn, (int)block.x, smem);
+    clear_stale_error();
     fn<<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
 }

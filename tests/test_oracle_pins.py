@@ -309,3 +309,111 @@ def test_golden_l12_matches_tm_rows_at_small_l():
     for ell in range(4):
         for k, lg in g[ell].items():
             assert math.isclose(lg, math.log(tm[k, ell]), abs_tol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Thermodynamics from g_kl (Eq. 2) against a direct sum over configurations
+# --------------------------------------------------------------------------
+
+def _direct_thermo(L, T, H):
+    """Z, <E>, C, <M>, <|M|>, chi per spin summed over all 2^N configurations
+    of the periodic LxL square lattice with E = -sum_bonds s_i s_j - H sum_i s_i."""
+    N = L * L
+    cfg = np.arange(2**N, dtype=np.int64)
+    s = 2 * ((cfg[:, None] >> np.arange(N)[None, :]) & 1).astype(np.int8) - 1
+    grid = s.reshape(-1, L, L).astype(np.int64)
+    bonds = (grid * np.roll(grid, 1, axis=2)).sum(axis=(1, 2)) + \
+            (grid * np.roll(grid, 1, axis=1)).sum(axis=(1, 2))
+    M = s.sum(axis=1).astype(np.float64)
+    out = []
+    for t in T:
+        row = []
+        for h in H:
+            E = -bonds.astype(np.float64) - h * M
+            x = -E / t
+            mx = x.max()
+            w = np.exp(x - mx)
+            z = w.sum()
+            e1, e2 = (w * E).sum() / z, (w * E * E).sum() / z
+            m1, ma, m2 = (w * M).sum() / z, (w * np.abs(M)).sum() / z, (w * M * M).sum() / z
+            row.append([(mx + np.log(z)) / N, e1 / N, (e2 - e1 * e1) / (t * t * N), m1 / N,
+                        ma / N, (m2 - m1 * m1) / (t * N)])
+        out.append(row)
+    return np.array(out)
+
+
+def test_thermo_matches_direct_configuration_sum():
+    g = oracle.brute_force(oracle.SQUARE, 4)
+    offs, lng = oracle.exact_surface(g)
+    T = np.array([0.8, 2.269, 3.5, 10.0])
+    H = np.array([-0.4, 0.0, 0.25, 1.0])
+    got = oracle.thermo(16, 32, offs, lng, T, H)
+    ref = _direct_thermo(4, T, H)
+    assert np.allclose(got, ref, rtol=1e-10, atol=1e-12)
+    # <E> = -d ln Z / d beta (finite difference at H = 0.25)
+    b0, db = 1 / 2.0, 1e-5
+    lz = [oracle.thermo(16, 32, offs, lng, np.array([1 / b]), np.array([0.25]))[0, 0, 0] * 16
+          for b in (b0 - db, b0 + db)]
+    e = oracle.thermo(16, 32, offs, lng, np.array([1 / b0]), np.array([0.25]))[0, 0, 1] * 16
+    assert math.isclose(-(lz[1] - lz[0]) / (2 * db), e, rel_tol=1e-6)
+
+
+# --------------------------------------------------------------------------
+# Open boundaries (the lattices of Fig. 2)
+# --------------------------------------------------------------------------
+
+def _numpy_open(L):
+    N = L * L
+    cfg = np.arange(2**N, dtype=np.int64)
+    spins = ((cfg[:, None] >> np.arange(N)[None, :]) & 1).astype(np.int8)
+    grid = spins.reshape(-1, L, L)
+    k = (grid[:, :, 1:] != grid[:, :, :-1]).sum(axis=(1, 2)) + \
+        (grid[:, 1:, :] != grid[:, :-1, :]).sum(axis=(1, 2))
+    g = np.zeros((2 * L * (L - 1) + 1, N + 1))
+    np.add.at(g, (k, spins.sum(axis=1)), 1)
+    return g
+
+
+def test_open_lattice_brute_force_and_closed_forms():
+    L, N, NB = 4, 16, 24
+    g = oracle.brute_force(oracle.SQUARE_OPEN, L)
+    assert np.array_equal(g, _numpy_open(L))
+    assert oracle.lattice_info(oracle.SQUARE_OPEN, L) == {"N": N, "NB": NB, "z": 4}
+    for l in range(N + 1):
+        assert g[:, l].sum() == math.comb(N, l)
+        assert np.array_equal(g[:, l], g[:, N - l])
+    # one up spin: k = its degree (4 corners, 4(L-2) edge sites, (L-2)^2 bulk sites)
+    assert (g[2, 1], g[3, 1], g[4, 1]) == (4, 4 * (L - 2), (L - 2) ** 2)
+    # l = N/2: lowest k = L, a straight interface (discussion of Fig. 2); Neel at k = N_B
+    col = g[:, N // 2]
+    assert col[:L].sum() == 0 and col[L] > 0 and col[NB] == 2
+    # odd k occur: bins of step 1
+    assert g[1::2].sum() > 0 and oracle.kstep(oracle.SQUARE_OPEN) == 1
+
+
+def test_open_lattice_walk_consistent_and_reaches_every_k():
+    g = oracle.brute_force(oracle.SQUARE_OPEN, 4)
+    for ell in range(9):
+        st = oracle.run_line(oracle.SQUARE_OPEN, 4, ell, 2, 1e-6, 1000)
+        assert st.converged and oracle.audit(st) == 0
+        assert set(np.nonzero(st.visited)[0]) == set(np.nonzero(g[:, ell])[0])
+
+
+def test_same_f_resets_keeps_the_walk_exact_and_accurate():
+    """The extra reset at unchanged f: R = 0 is the base algorithm bit for bit;
+    with R = 2 the walk stays consistent and still reaches exact values."""
+    a = oracle.run_line(oracle.SQUARE, 6, 12, 5, 1e-6, 1000, budget=300_000)
+    b = oracle.run_line(oracle.SQUARE, 6, 12, 5, 1e-6, 1000, budget=300_000, same_f_resets=0)
+    assert np.array_equal(a.lng, b.lng) and np.array_equal(a.sc, b.sc)
+    c = oracle.run_line(oracle.SQUARE, 6, 12, 5, 1e-6, 1000, budget=300_000, same_f_resets=2)
+    assert oracle.audit(c) == 0 and not np.array_equal(a.lng, c.lng)
+    g = oracle.brute_force(oracle.SQUARE, 4)
+    errs = []
+    for seed in range(1, 5):
+        for ell in range(2, 9):
+            st = oracle.run_line(oracle.SQUARE, 4, ell, seed, 1e-8, 10**5, same_f_resets=2)
+            lg = oracle.assemble(16, ell, st.lng, st.visited, 1e-8)
+            ks = np.nonzero(g[:, ell])[0]
+            errs.append(np.abs(lg[ks // 2] - np.log(g[ks, ell])))
+    errs = np.concatenate(errs)
+    assert errs.mean() <= 0.05

@@ -51,7 +51,7 @@ class Buffers:
         self.perm = torch.zeros(nlines * self.P, dtype=torch.int16 if isz == 2 else torch.int32, device=dev)
         self.spins = torch.zeros(nlines * self.W, dtype=torch.int32, device=dev)
         self.lng = torch.zeros(int(self.off[-1]), dtype=torch.int64, device=dev)
-        self.hist = torch.zeros(int(self.off[-1]), dtype=torch.int32, device=dev)
+        self.hist = torch.zeros(int(self.off[-1]), dtype=torch.int64, device=dev)
         self.state = torch.zeros(nlines * 9, dtype=torch.int64, device=dev)
         self.stream = torch.cuda.current_stream().cuda_stream
 
@@ -64,13 +64,13 @@ class Buffers:
         perm = self.perm.cpu().numpy().view(np.uint16 if self.perm.element_size() == 2 else np.uint32)
         words = self.spins.cpu().numpy().view(np.uint32)[i * self.W:(i + 1) * self.W]
         spins = ((words[np.arange(N) >> 5] >> (np.arange(N) & 31)) & 1).astype(np.uint8)
-        h = self.hist.cpu().numpy().view(np.uint32)[self.off[i]:self.off[i + 1]]
+        h = self.hist.cpu().numpy().view(np.uint64)[self.off[i]:self.off[i + 1]]
         return {"sc": self.state.cpu().numpy()[i * 9:i * 9 + 8],
                 "perm": perm[i * self.P:i * self.P + N].astype(np.int32),
                 "spins": spins,
                 "lng": self.lng.cpu().numpy()[self.off[i]:self.off[i + 1]],
-                "hist": (h & 0x7FFFFFFF).astype(np.int64),
-                "visited": (h >> 31).astype(np.uint8)}
+                "hist": (h & np.uint64(0x7FFFFFFFFFFFFFFF)).astype(np.int64),
+                "visited": (h >> np.uint64(63)).astype(np.uint8)}
 
 
 @pytest.mark.parametrize("lattice,L,ell_first,nlines", [("square", 8, 0, 33), ("triangular", 6, 3, 8)])
