@@ -355,3 +355,15 @@ def test_production_accuracy_square_L12_against_transfer_matrix():
     assert small.mean() <= 0.02 and small.max() <= 0.6
     assert large.mean() <= 0.05 and large.max() <= 1.5
     assert ends.mean() <= 0.5
+
+
+def test_square_L256_sampled_lines():
+    """256x256 (32769 lines, lists in global memory, spins staged): sampled
+    lines after 16384 moves each, against the oracle."""
+    budget = 16384
+    h = run_gpu("square", 256, 2, 1e-6, 4096, budget)
+    ells = [1, 3, 4000, 16384, 32767, 32768]
+    ref = oracle_lines(oracle.SQUARE, 256, ells, 2, 1e-6, 4096, budget)
+    for ell in ells:
+        assert_line_equal(h, ell, ref[ell], "L256")
+    h.close()
