@@ -358,7 +358,7 @@ def test_production_accuracy_square_L12_against_transfer_matrix():
 
 
 def test_square_L256_sampled_lines():
-    """256x256 (32769 lines, lists in global memory, spins staged): sampled
+    """256x256 (32769 lines, lists and spins in global memory): sampled
     lines after 16384 moves each, against the oracle."""
     budget = 16384
     h = run_gpu("square", 256, 2, 1e-6, 4096, budget)
