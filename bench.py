@@ -139,6 +139,49 @@ def walker_traffic(moves_per_line: int, mapping: int):
     return None
 
 
+def sum_over_lines(lines, N: int, kstep: int = 2):
+    """ln g_k = ln sum_l g_kl from the assembled lines l = 0..N/2 (ln g_kl over
+    k = 0, kstep, ...; -inf where unvisited), lines l > N/2 by the l <-> N - l
+    mirror: the sum the paper compares with the exact zero-field g_k (Sec. 4,
+    Fig. 5)."""
+    import numpy as np
+    width = max(len(v) for v in lines)
+    mat = np.full((N + 1, width), -np.inf)
+    for ell, v in enumerate(lines):
+        mat[ell, :len(v)] = v
+        mat[N - ell, :len(v)] = v
+    top = mat.max(axis=0)
+    out = np.full(width, -np.inf)
+    fin = np.isfinite(top)
+    out[fin] = top[fin] + np.log(np.exp(mat[:, fin] - top[fin]).sum(axis=0))
+    full = np.full((width - 1) * kstep + 1, -np.inf)
+    full[::kstep] = out
+    return full
+
+
+def exact_gk_comparison(lng_k, path: str, NB: int):
+    """Differences between a summed surface and the stored exact zero-field
+    ln g_k (columns k, ln g_k): |d ln g_k| and |dS_k| with S_k = ln g_k / N_B
+    (the quantity of Fig. 5), over every k with g_k > 0 and over the inner k
+    (without the two lowest and two highest energies of the spectrum)."""
+    import numpy as np
+    ex = np.full(NB + 1, -np.inf)
+    for k, v in np.loadtxt(path, ndmin=2):
+        ex[int(k)] = v
+    got = np.full(NB + 1, -np.inf)
+    got[:min(len(lng_k), NB + 1)] = lng_k[:NB + 1]
+    ks = np.nonzero(np.isfinite(ex))[0]
+    missing = int((~np.isfinite(got[ks])).sum())
+    ks = ks[np.isfinite(got[ks])]
+    d = np.abs(got[ks] - ex[ks])
+    inner = d[2:-2] if d.size > 4 else d
+    return {"exact": os.path.relpath(path, ROOT), "k_compared": int(ks.size), "k_missing": missing,
+            "max_abs_dlng": float(d.max()), "mean_abs_dlng": float(d.mean()),
+            "max_abs_dS": float(d.max() / NB), "mean_abs_dS": float(d.mean() / NB),
+            "inner_max_abs_dS": float(inner.max() / NB),
+            "worst_k": int(ks[int(np.argmax(d))])}
+
+
 def run_converge(args):
     """Time to ln f_min: one whole surface walked until every line converged
     (or the time limit), reported as its own JSON line."""
@@ -160,6 +203,12 @@ def run_converge(args):
             "min_stage": st["min_stage"], "max_stage": st["max_stage"], "moves": st["moves"],
             "moves_per_s": st["moves"] / sec, "mapping": st["mapping"],
             "accept_rate": st["accepts"] / max(st["moves"], 1)}
+    exact = os.path.join(ROOT, "tests", "golden", f"square_L{Lc}_gk_exact.txt")
+    if lat == "square" and os.path.exists(exact):
+        h.assemble()
+        lines = [h.get_lng(ell) for ell in range(h.N // 2 + 1)]
+        line["sum_over_lines_vs_exact_gk"] = exact_gk_comparison(
+            sum_over_lines(lines, h.N), exact, 2 * h.N)
     print(json.dumps(line), flush=True)
     h.close()
     return 0

@@ -8,6 +8,10 @@ site-by-site transfer matrix (the exact surface that Eq. 2 sums over; the
 paper cites transfer-matrix surfaces up to 12x12).  Columns: l, k, ln g_kl.
 cubic_L3_exact.txt: exact g_kl of the periodic 3x3x3 simple cubic lattice by
 enumeration of all 2^27 configurations.  Columns: l, k, g_kl.
+square_L{16,32,64}_gk_exact.txt: exact zero-field ln g_k of the periodic L x L
+square lattice from Kaufman's partition function (oracle/exact_gk.py), the
+values the paper compares its summed surfaces with (Sec. 4, Fig. 5).  Columns:
+k, ln g_k (k with g_k > 0 only).
 """
 import argparse
 import math
@@ -51,12 +55,29 @@ def write_cubic_l3():
     print(f"cubic L=3: {time.time() - t0:.1f} s -> {path}")
 
 
+def write_square_gk(L):
+    from oracle import exact_gk
+    t0 = time.time()
+    lg = exact_gk.ln_gk(L)
+    path = os.path.join(HERE, f"square_L{L}_gk_exact.txt")
+    with open(path, "w") as f:
+        f.write(f"# exact zero-field ln g_k, periodic {L}x{L} square lattice, Kaufman's "
+                "partition function (tests/golden/make_golden.py)\n# k ln_g\n")
+        for k in range(lg.size):
+            if np.isfinite(lg[k]):
+                f.write(f"{k} {lg[k]:.17g}\n")
+    print(f"square g_k L={L}: {time.time() - t0:.1f} s -> {path}")
+
+
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--threads", type=int, default=os.cpu_count() or 1)
-    ap.add_argument("--only", choices=["square", "cubic"], default=None)
+    ap.add_argument("--only", choices=["square", "cubic", "gk"], default=None)
     a = ap.parse_args()
     if a.only in (None, "cubic"):
         write_cubic_l3()
     if a.only in (None, "square"):
         write_square_l12(a.threads)
+    if a.only in (None, "gk"):
+        for L in (16, 32, 64):
+            write_square_gk(L)
