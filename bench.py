@@ -190,14 +190,14 @@ def run_converge(args):
     lat, Lc = args.lattice, args.converge
     h = wl.Handle(lat, Lc, deterministic=1, check_interval=args.check_interval, seed=1,
                   mapping=args.mapping, timeout_ms=int(args.time_limit * 1000),
-                  same_f_resets=args.same_f_resets)
+                  same_f_resets=args.same_f_resets, resolve=args.resolve)
     t0 = time.perf_counter()
     rc = h.run(args.ln_f_min, FLATNESS, allow=(wl.WL_OK, wl.WL_ETIMEOUT))
     sec = time.perf_counter() - t0
     st = h.stats()
     line = {"mode": "time_to_ln_f_min", "lattice": lat, "L": Lc, "N": h.N, "lines": st["lines"],
             "ln_f_min": args.ln_f_min, "check_interval": args.check_interval,
-            "same_f_resets": args.same_f_resets,
+            "same_f_resets": args.same_f_resets, "resolve": args.resolve,
             "status": "converged" if rc == wl.WL_OK else "time limit",
             "seconds": sec, "lines_converged": st["lines_converged"],
             "min_stage": st["min_stage"], "max_stage": st["max_stage"], "moves": st["moves"],
@@ -404,7 +404,8 @@ def run_ours(args):
 
     h = wl.Handle(LATTICE, L, deterministic=1, check_interval=CHECK_INTERVAL,
                   move_budget=args.moves_per_line, slice_moves=args.moves_per_line,
-                  mapping=args.mapping, form=args.form, stream=stream.cuda_stream)
+                  mapping=args.mapping, form=args.form, stream=stream.cuda_stream,
+                  resolve=args.resolve)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
 
     def step(seed):
@@ -540,6 +541,8 @@ def main():
     ap.add_argument("--check-interval", type=int, default=CHECK_INTERVAL)
     ap.add_argument("--time-limit", type=float, default=600.0, help="seconds, --converge only")
     ap.add_argument("--same-f-resets", type=int, default=0, help="extra same-f resets per stage")
+    ap.add_argument("--resolve", type=int, default=0, choices=[0, 1, 2],
+                    help="batch resolution: 0 by acceptance rate, 1 single steps, 2 rounds")
     ap.add_argument("--serve", type=int, default=0, help="run the serving benchmark with N requests")
     ap.add_argument("--serve-moves", type=int, default=1 << 22, help="per-line move budget of a request")
     ap.add_argument("--max-active", type=int, default=8)

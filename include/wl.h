@@ -106,6 +106,11 @@ size_t wl_required_bytes(wl_lattice lattice, int L);
  *                    while ln f is kept -- the extra reset the paper remarks
  *                    after Eq. 4 speeds the walk; its trigger is not given
  *                    there, this is one choice (default 0: off)
+ *   "resolve"        how a walker resolves a batch of speculative proposals:
+ *                    1 steps one at a time, 2 rounds that commit every
+ *                    rejection up to the next accepted step at once, 0 picks
+ *                    per walker from its recent acceptance rate (default 0).
+ *                    The chain is the same in all three; only speed differs.
  * Setting "seed", "deterministic", "check_interval", "same_f_resets" or the
  * line range after a run requires wl_reset().  Errors: WL_EINVAL (unknown key or bad value), WL_ESTATE. */
 wl_status wl_set_option(wl_handle h, const char* key, int64_t value);

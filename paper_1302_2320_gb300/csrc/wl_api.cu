@@ -352,6 +352,7 @@ WalkArgs base_args(wl_ctx* h)
     a.flat_pm = h->flat_pm;
     a.pstride = h->lo.pstride;
     a.same_f_resets = h->same_f_resets;
+    a.resolve = h->resolve;
     a.C = h->C;
     a.budget = h->budget;
     a.slice_moves = h->slice_moves;
@@ -771,6 +772,9 @@ wl_status wl_set_option(wl_handle h, const char* key, int64_t v)
     } else if (k == "same_f_resets") {
         if (v < 0 || v > 1000000) return fail(WL_EINVAL, "same_f_resets must be in [0, 10^6]");
         h->same_f_resets = (int)v;
+    } else if (k == "resolve") {
+        if (v < 0 || v > 2) return fail(WL_EINVAL, "resolve must be 0, 1 or 2");
+        h->resolve = (int)v;
     } else if (k == "ell_min" || k == "ell_max") {
         if (v < 0 || v >= h->lo.nlines) return fail(WL_EINVAL, "%s must be in [0, %d]", key, h->lo.nlines - 1);
         (k == "ell_min" ? h->ell_min : h->ell_max) = (int)v;
@@ -796,6 +800,7 @@ wl_status wl_get_option(wl_handle h, const char* key, int64_t* v)
     else if (k == "hbm_budget") *v = h->hbm_budget;
     else if (k == "ell_min") *v = h->ell_min;
     else if (k == "same_f_resets") *v = h->same_f_resets;
+    else if (k == "resolve") *v = h->resolve;
     else if (k == "ell_max") *v = h->ell_max;
     else if (k == "N") *v = h->g.N;
     else if (k == "NB") *v = h->g.NB;

@@ -53,6 +53,7 @@ struct wl_ctx {
     int64_t hbm_budget = 0;
     int ell_min = 0, ell_max = 0;
     int same_f_resets = 0;
+    int resolve = 0;
     // state
     bool allocated = false, initialized = false, assembled = false;
     double u = 0.0;

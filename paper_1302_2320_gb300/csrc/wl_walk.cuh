@@ -7,12 +7,16 @@
 //     exchange proposal against the state at the start of the batch: list
 //     slots a, b, sites i = U[a], j = D[b], their neighbours and the change of
 //     k (all of this is independent of the acceptance decisions);
-//   serial scan -- the group resolves the steps in order with Eq. 3 against the
-//     current k and ln g (every lane computes the same scan state).  An accepted
-//     exchange of (i_s, j_s) leaves a later proposal exact unless it reuses list
-//     slot a_s or b_s or has i_s or j_s among its sites' neighbours; such
-//     proposals are marked, and the batch ends at the first marked one (or
-//     when a proposal's bin leaves the group's ln g window).
+//   resolution -- the group resolves the steps in order with Eq. 3 against
+//     the current k and ln g (every lane holds the same walker state).  While
+//     the walker stays in its bin, step m sees the ln g of step e0 plus F for
+//     each step in between, so all lanes test their own step at once; a ballot
+//     finds the first accepted step, the rejections before it are committed
+//     together, and the lanes are re-tested only when an accepted step changes
+//     the bin.  An accepted exchange of (i_s, j_s) leaves a later proposal
+//     exact unless it reuses list slot a_s or b_s or has i_s or j_s among its
+//     sites' neighbours; such proposals are marked, and the batch ends at the
+//     first marked one (or when a proposal's bin leaves the ln g window).
 // The accepted exchanges of a batch are mutually independent and are applied
 // together after the scan.  Random numbers are keyed by t, so the committed
 // chain is the sequential chain, bit for bit, for every S.  Batches never cross
@@ -32,6 +36,15 @@ __device__ __forceinline__ unsigned group_mask(int gbase)
 {
     if constexpr (S == 32) return 0xffffffffu;
     else return ((1u << S) - 1u) << gbase;
+}
+
+// The predicate of each lane of the group as bits 0 .. S-1.
+template <int S>
+__device__ __forceinline__ unsigned group_ballot(unsigned gmask, int gbase, bool p)
+{
+    const unsigned b = __ballot_sync(gmask, p);
+    if constexpr (S == 32) return b;
+    else return (b >> gbase) & ((1u << S) - 1u);
 }
 
 // Flatness (80%/80% convention, fraction x = flat_pm/1000, exact integers):
@@ -163,6 +176,8 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
     hist_t hcur = wh[bc - wb];
     uint32_t pend = 0;
     int stop = 0;
+    bool by_rounds = false;               // resolution chosen from the acceptance rate
+    int rate_acc = 0, rate_steps = 0;
 
     uint4 r0 = philox_step((uint64_t)(t + m), key);
     uint4 r1 = make_uint4(0u, 0u, 0u, 0u);
@@ -189,80 +204,184 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
             uint32_t ni[zc], nj[zc];
             const int dk = delta_k_nb<LAT>(A.g, sp, i, j, ni, nj);
             if (needf) r1 = rf;
-            // -- serial phase: the steps in order with Eq. 3 against the current
-            //    k and ln g.  An accepted exchange of (i_s, j_s) leaves a later
-            //    proposal exact unless it reuses list slot a_s or b_s or one of
-            //    i_s, j_s neighbours its sites; such proposals are marked, and the
-            //    batch ends at the first marked one.
+            // -- resolution: the steps in order with Eq. 3 against the current k
+            //    and ln g (every lane holds the same walker state).  An accepted
+            //    exchange of (i_s, j_s) leaves a later proposal exact unless it
+            //    reuses list slot a_s or b_s or one of i_s, j_s neighbours its
+            //    sites; such proposals are marked, and the batch ends at the
+            //    first marked one.  Two equivalent ways, chosen per walker:
             unsigned inv = 0u, accm = 0u;
             int c = lim;
-            // step s's change of k and random word, shuffled one step ahead
-            int dkn = __shfl_sync(gmask, dk, gbase);
-            uint32_t rzn = __shfl_sync(gmask, r0.z, gbase);
-            for (int s = 0; s < lim; ++s) {
-                const int src = gbase + s;
-                const int dks = dkn;
-                const uint32_t rzs = rzn;
-                const int nxt = gbase + (s + 1 < S ? s + 1 : s);
-                dkn = __shfl_sync(gmask, dk, nxt);
-                rzn = __shfl_sync(gmask, r0.z, nxt);
-                if ((inv >> s) & 1u) {
-                    c = s;
-                    break;
-                }
-                const int kp = (int)k + dks;
-                bool acc = true;
-                int64_t lp = 0;
-                if (dks != 0) {
-                    const int bp = kp >> ks;
-                    const int wx = bp - wb;
-                    if ((unsigned)bp >= (unsigned)nbins) {      // invariant broken
+            if (A.resolve == 2 || (A.resolve == 0 && by_rounds)) {
+                // Rounds.  While the walker keeps its bin, step m sees the state
+                // of step e0 with F added once per step in between (a rejection
+                // or an accepted exchange with dk = 0 both visit the current
+                // bin), so every lane tests its own step at once.  The first lane
+                // that accepts, leaves the window or was marked ends the round,
+                // and the rejections before it are committed together.  Lanes
+                // are tested again only after an accepted step changes the bin.
+                const unsigned live = lim >= 32 ? 0xffffffffu : ((1u << lim) - 1u);
+                unsigned evb = 0u;
+                int pk = 0;                // (dk + 64) << 2 | kind of this lane's step
+                long long lpm = 0;         // ln g of its target bin
+                int e0 = 0;
+                bool eval = true;
+                for (int round = 0; ; ++round) {
+                    if (round > S) {       // cannot happen: e0 grows every round
                         stop = 4;
-                        c = s;
+                        c = e0;
                         break;
                     }
-                    if ((unsigned)wx >= (unsigned)wn) {        // walked off the window
-                        c = s;
+                    if (eval) {
+                        // kind: 0 accepted, 1 off the window, 2 outside the line, -1 rejected
+                        int kind = 0;
+                        if (dk != 0) {
+                            const int bp = ((int)k + dk) >> ks;
+                            const int wx = bp - wb;
+                            if ((unsigned)bp >= (unsigned)nbins) {
+                                kind = 2;
+                            } else if ((unsigned)wx >= (unsigned)wn) {
+                                kind = 1;
+                            } else {
+                                lpm = wl[wx];
+                                const int64_t d = lpm - (cur + (int64_t)(m - e0) * F);
+                                const bool acc = d <= 0 ||
+                                                 accept_uphill<DET>(d, r0.z, tab, A.q, A.neg_u_log2e);
+                                kind = acc ? 0 : -1;
+                            }
+                        }
+                        pk = ((dk + 64) << 2) | (kind & 3);
+                        evb = group_ballot<S>(gmask, gbase, kind >= 0);
+                        eval = false;
+                    }
+                    const unsigned ev = (evb | inv) & live & ~((1u << e0) - 1u);
+                    if (ev == 0u) {        // the rest of the batch is rejected
+                        cur += (int64_t)(lim - e0) * F;
+                        pend += (uint32_t)(lim - e0);
                         break;
                     }
-                    lp = wl[wx];
-                    const int64_t d = lp - cur;
-                    acc = d <= 0 || accept_uphill<DET>(d, rzs, tab, A.q, A.neg_u_log2e);
-                }
-                if (!acc) {
-                    cur += F;
-                    pend += 1u;
-                    continue;
-                }
-                accm |= 1u << s;
-                if (dks != 0) {
-                    // leave the current bin: its ln g and histogram go to the window
-                    if ((hcur & ~kVisited) + pend >= kVisited) stop = 2;
-                    if (pend) hcur = (hcur + pend) | kVisited;
-                    wl[bc - wb] = cur;
-                    wh[bc - wb] = hcur;
-                    k = kp;
-                    bc = kp >> ks;
-                    cur = lp + F;
-                    hcur = wh[bc - wb];
-                    pend = 1u;
-                } else {
-                    cur += F;
-                    pend += 1u;
-                }
-                // later proposals that the accepted exchange of (i_s, j_s) affects
-                const uint32_t as = __shfl_sync(gmask, a, src), bs = __shfl_sync(gmask, b, src);
-                const uint32_t is = __shfl_sync(gmask, i, src), js = __shfl_sync(gmask, j, src);
-                bool conf = (a == as) | (b == bs);
+                    const int e = __ffs(ev) - 1;
+                    cur += (int64_t)(e - e0) * F;      // rejections e0 .. e-1
+                    pend += (uint32_t)(e - e0);
+                    const unsigned bit = 1u << e;
+                    if (inv & bit) {
+                        c = e;
+                        break;
+                    }
+                    const int src = gbase + e;
+                    const int code = __shfl_sync(gmask, pk, src);
+                    const int64_t lpe = __shfl_sync(gmask, lpm, src);
+                    if ((code & 3) == 2) {             // invariant broken
+                        stop = 4;
+                        c = e;
+                        break;
+                    }
+                    if ((code & 3) == 1) {             // walked off the window
+                        c = e;
+                        break;
+                    }
+                    accm |= bit;
+                    const int dke = (code >> 2) - 64;
+                    if (dke != 0) {
+                        // leave the current bin: its ln g and histogram go to the window
+                        const int kp = (int)k + dke;
+                        if ((hcur & ~kVisited) + pend >= kVisited) stop = 2;
+                        if (pend) hcur = (hcur + pend) | kVisited;
+                        wl[bc - wb] = cur;
+                        wh[bc - wb] = hcur;
+                        k = kp;
+                        bc = kp >> ks;
+                        cur = lpe + F;
+                        hcur = wh[bc - wb];
+                        pend = 1u;
+                        eval = true;
+                    } else {
+                        cur += F;
+                        pend += 1u;
+                    }
+                    // later proposals that the accepted exchange of (i_e, j_e) affects
+                    const uint32_t as = __shfl_sync(gmask, a, src), bs = __shfl_sync(gmask, b, src);
+                    const uint32_t is = __shfl_sync(gmask, i, src), js = __shfl_sync(gmask, j, src);
+                    bool conf = (a == as) | (b == bs);
 #pragma unroll
-                for (int q = 0; q < zc; ++q)
-                    conf |= (ni[q] == is) | (ni[q] == js) | (nj[q] == is) | (nj[q] == js);
-                unsigned cb = __ballot_sync(gmask, conf && m > s);
-                if constexpr (S < 32) cb = (cb >> gbase) & ((1u << S) - 1u);
-                inv |= cb;
-                if (stop) {
-                    c = s + 1;
-                    break;
+                    for (int q = 0; q < zc; ++q)
+                        conf |= (ni[q] == is) | (ni[q] == js) | (nj[q] == is) | (nj[q] == js);
+                    inv |= group_ballot<S>(gmask, gbase, conf && m > e);
+                    e0 = e + 1;
+                    if (stop) {
+                        c = e0;
+                        break;
+                    }
+                    if (e0 >= lim) break;
+                }
+            } else {
+                // Steps one at a time; step s's change of k and random word are
+                // shuffled one step ahead.
+                int dkn = __shfl_sync(gmask, dk, gbase);
+                uint32_t rzn = __shfl_sync(gmask, r0.z, gbase);
+                for (int s = 0; s < lim; ++s) {
+                    const int src = gbase + s;
+                    const int dks = dkn;
+                    const uint32_t rzs = rzn;
+                    const int nxt = gbase + (s + 1 < S ? s + 1 : s);
+                    dkn = __shfl_sync(gmask, dk, nxt);
+                    rzn = __shfl_sync(gmask, r0.z, nxt);
+                    if ((inv >> s) & 1u) {
+                        c = s;
+                        break;
+                    }
+                    const int kp = (int)k + dks;
+                    bool acc = true;
+                    int64_t lp = 0;
+                    if (dks != 0) {
+                        const int bp = kp >> ks;
+                        const int wx = bp - wb;
+                        if ((unsigned)bp >= (unsigned)nbins) {      // invariant broken
+                            stop = 4;
+                            c = s;
+                            break;
+                        }
+                        if ((unsigned)wx >= (unsigned)wn) {        // walked off the window
+                            c = s;
+                            break;
+                        }
+                        lp = wl[wx];
+                        const int64_t d = lp - cur;
+                        acc = d <= 0 || accept_uphill<DET>(d, rzs, tab, A.q, A.neg_u_log2e);
+                    }
+                    if (!acc) {
+                        cur += F;
+                        pend += 1u;
+                        continue;
+                    }
+                    accm |= 1u << s;
+                    if (dks != 0) {
+                        // leave the current bin: its ln g and histogram go to the window
+                        if ((hcur & ~kVisited) + pend >= kVisited) stop = 2;
+                        if (pend) hcur = (hcur + pend) | kVisited;
+                        wl[bc - wb] = cur;
+                        wh[bc - wb] = hcur;
+                        k = kp;
+                        bc = kp >> ks;
+                        cur = lp + F;
+                        hcur = wh[bc - wb];
+                        pend = 1u;
+                    } else {
+                        cur += F;
+                        pend += 1u;
+                    }
+                    // later proposals that the accepted exchange of (i_s, j_s) affects
+                    const uint32_t as = __shfl_sync(gmask, a, src), bs = __shfl_sync(gmask, b, src);
+                    const uint32_t is = __shfl_sync(gmask, i, src), js = __shfl_sync(gmask, j, src);
+                    bool conf = (a == as) | (b == bs);
+#pragma unroll
+                    for (int q = 0; q < zc; ++q)
+                        conf |= (ni[q] == is) | (ni[q] == js) | (nj[q] == is) | (nj[q] == js);
+                    inv |= group_ballot<S>(gmask, gbase, conf && m > s);
+                    if (stop) {
+                        c = s + 1;
+                        break;
+                    }
                 }
             }
             if (c == 0) stop = 4;                  // lane 0 is always evaluable
@@ -274,6 +393,14 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
                 atomicOr(&sp[j >> 5], 1u << (j & 31u));
             }
             accepts += __popc(accm);
+            // rounds pay per accepted step, single steps per step: pick rounds
+            // while fewer than half of the recent steps were accepted
+            rate_acc += __popc(accm);
+            rate_steps += c;
+            if (rate_steps >= 512) {
+                by_rounds = 2 * rate_acc < rate_steps;
+                rate_acc = rate_steps = 0;
+            }
             __syncwarp(gmask);
             if ((bc - zb < wb && wb > 0) || (bc + zb >= wb + kWin && wb + kWin < nbins)) {
                 // re-centre the window (the current bin stays in registers)

@@ -143,6 +143,29 @@ def test_other_lattices_bit_exact(lattice, L, budget):
         assert_line_equal(h, ell, ref[ell], lattice)
 
 
+@pytest.mark.parametrize("resolve", [1, 2])
+@pytest.mark.parametrize("mapping", [1, 8, 32])
+def test_square_L12_bit_exact_each_resolution(l12_ref, resolve, mapping):
+    """Both ways of resolving a batch (one step at a time; rounds that commit
+    the rejections up to the next accepted step at once), forced for the whole
+    walk, give the oracle's chain."""
+    h = run_gpu("square", 12, 1, 1e-8, 1000, 10**7, mapping=mapping, resolve=resolve)
+    for ell in range(73):
+        assert_line_equal(h, ell, l12_ref[ell], f"S={mapping} resolve={resolve}")
+
+
+@pytest.mark.parametrize("resolve", [1, 2])
+@pytest.mark.parametrize("lattice,L,mapping", [("triangular", 6, 32), ("cubic", 4, 8),
+                                               ("square_open", 7, 32), ("square_open", 16, 4)])
+def test_other_lattices_each_resolution(lattice, L, mapping, resolve):
+    budget = 300_000
+    h = run_gpu(lattice, L, 9, 1e-6, 777, budget, mapping=mapping, resolve=resolve)
+    N = h.N
+    ref = oracle_lines(LAT[lattice], L, range(N // 2 + 1), 9, 1e-6, 777, budget)
+    for ell in range(N // 2 + 1):
+        assert_line_equal(h, ell, ref[ell], f"{lattice} resolve={resolve}")
+
+
 def test_square_L64_sampled_lines_bench_launch():
     """The L=64 workload in the benchmark's launch shape (autotuned mapping,
     persistent form, slices): sampled lines against the oracle."""
