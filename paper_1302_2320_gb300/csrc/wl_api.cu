@@ -492,8 +492,8 @@ int kernel_lattice(const wl_ctx* h)
     return h->g.type;
 }
 
-// 32 lanes per walker: on the 64x64 lattice the acceptance scan commits ~20
-// moves per batch and this mapping was fastest for every lattice measured.
+// 32 lanes per walker: on the 64x64 lattice a batch commits ~20 moves and this
+// mapping was fastest for every lattice measured.
 int pick_mapping_default(const wl_ctx*)
 {
     return 32;

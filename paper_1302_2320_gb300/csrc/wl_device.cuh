@@ -71,7 +71,7 @@ struct WalkArgs {
     int32_t slot_bytes;      // shared bytes per walker slot (window + staged list/spins)
     int32_t pstride;         // list entries per line, N rounded up to 16 bytes
     int32_t same_f_resets;   // R > 0: extra histogram resets at unchanged f (see walk_line)
-    int32_t resolve;         // batch resolution: 0 by acceptance rate, 1 step scan, 2 rounds
+    int32_t resolve;         // batch resolution: 0 by acceptance rate, 1 single steps, 2 rounds
     int64_t C;               // flatness check interval
     int64_t budget;          // per-line cap on t
     int64_t slice_moves;     // moves per line in this launch

@@ -8,17 +8,19 @@
 //     slots a, b, sites i = U[a], j = D[b], their neighbours and the change of
 //     k (all of this is independent of the acceptance decisions);
 //   resolution -- the group resolves the steps in order with Eq. 3 against
-//     the current k and ln g (every lane holds the same walker state).  While
-//     the walker stays in its bin, step m sees the ln g of step e0 plus F for
-//     each step in between, so all lanes test their own step at once; a ballot
-//     finds the first accepted step, the rejections before it are committed
-//     together, and the lanes are re-tested only when an accepted step changes
-//     the bin.  An accepted exchange of (i_s, j_s) leaves a later proposal
-//     exact unless it reuses list slot a_s or b_s or has i_s or j_s among its
-//     sites' neighbours; such proposals are marked, and the batch ends at the
-//     first marked one (or when a proposal's bin leaves the ln g window).
+//     the current k and ln g (every lane holds the same walker state), either
+//     one step at a time, or in rounds: while the walker stays in its bin,
+//     step m sees the ln g of step e0 plus F for each step in between, so all
+//     lanes test their own step at once, a ballot finds the first accepted
+//     step, the rejections before it are committed together, and the lanes
+//     are re-tested only when an accepted step changes the bin.  Each walker
+//     takes rounds while fewer than half of its recent steps were accepted.
+//     An accepted exchange of (i_s, j_s) leaves a later proposal exact unless
+//     it reuses list slot a_s or b_s or has i_s or j_s among its sites'
+//     neighbours; such proposals are marked, and the batch ends at the first
+//     marked one (or when a proposal's bin leaves the ln g window).
 // The accepted exchanges of a batch are mutually independent and are applied
-// together after the scan.  Random numbers are keyed by t, so the committed
+// together after the resolution.  Random numbers are keyed by t, so the committed
 // chain is the sequential chain, bit for bit, for every S.  Batches never cross
 // a flatness check (t multiple of C) or the end of the slice.
 //
@@ -233,23 +235,18 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
                         break;
                     }
                     if (eval) {
-                        // kind: 0 accepted, 1 off the window, 2 outside the line, -1 rejected
-                        int kind = 0;
-                        if (dk != 0) {
-                            const int bp = ((int)k + dk) >> ks;
-                            const int wx = bp - wb;
-                            if ((unsigned)bp >= (unsigned)nbins) {
-                                kind = 2;
-                            } else if ((unsigned)wx >= (unsigned)wn) {
-                                kind = 1;
-                            } else {
-                                lpm = wl[wx];
-                                const int64_t d = lpm - (cur + (int64_t)(m - e0) * F);
-                                const bool acc = d <= 0 ||
-                                                 accept_uphill<DET>(d, r0.z, tab, A.q, A.neg_u_log2e);
-                                kind = acc ? 0 : -1;
-                            }
-                        }
+                        // kind: 0 accepted, 1 off the window, 2 outside the line,
+                        // -1 rejected; without branches (a bin outside the window
+                        // reads the current bin's slot, always inside, and is
+                        // not used; dk = 0 is accepted)
+                        const int bp = ((int)k + dk) >> ks;
+                        const int wx = bp - wb;
+                        const bool brk = (unsigned)bp >= (unsigned)nbins;
+                        const bool off = (unsigned)wx >= (unsigned)wn;
+                        lpm = wl[(brk || off) ? bc - wb : wx];
+                        const int64_t d = lpm - (cur + (int64_t)(m - e0) * F);
+                        const bool up = accept_uphill<DET>(d, r0.z, tab, A.q, A.neg_u_log2e);
+                        const int kind = dk == 0 ? 0 : brk ? 2 : off ? 1 : (d <= 0 || up) ? 0 : -1;
                         pk = ((dk + 64) << 2) | (kind & 3);
                         evb = group_ballot<S>(gmask, gbase, kind >= 0);
                         eval = false;
