@@ -6,7 +6,10 @@ The exact g_k is pinned by things other than itself: full enumeration (4x4),
 the oracle's transfer matrix (6x6, 8x8 and the stored 12x12 surface, summed
 over l), and closed forms that hold at every even L (g_0 = 2, one flipped spin
 g_4 = 2N, two adjacent flipped spins g_6 = 4N, sum_k g_k = 2^N, g_k = g_{N_B-k}
-on a bipartite lattice, no odd k, no k = 2)."""
+on a bipartite lattice, no odd k, no k = 2) or at every L >= 5: g_8 = N^2 + 9N,
+the configurations of 8 unsatisfied bonds being two non-adjacent flipped spins
+(C(N,2) - 2N), straight and bent three-spin clusters (2N + 4N) and 2x2 blocks
+(N), twice for the global flip."""
 import math
 import os
 
@@ -76,6 +79,7 @@ def _closed_forms(lg, L, tol):
     assert abs(lg[0] - math.log(2)) < tol
     assert abs(lg[4] - math.log(2 * N)) < tol
     assert abs(lg[6] - math.log(4 * N)) < tol
+    assert abs(lg[8] - math.log(N * N + 9 * N)) < tol
     assert abs(_logsumexp(lg) - N * math.log(2)) < tol
     fin = np.isfinite(lg)
     assert np.array_equal(fin, fin[::-1])
@@ -87,6 +91,36 @@ def _closed_forms(lg, L, tol):
 @pytest.mark.parametrize("L", [16, 32])
 def test_closed_forms(L):
     _closed_forms(exact_gk.ln_gk(L), L, 1e-9)
+
+
+def test_g8_closed_form_small_lattices():
+    for L in (5, 6):
+        g = oracle.tm_square(L).sum(axis=1)
+        assert g[8] == L ** 4 + 9 * L * L
+
+
+def test_thermo_of_the_exact_surface_matches_kaufman_L12():
+    """Eq. 2 thermodynamics (the oracle's) of the stored 12x12 transfer-matrix
+    surface at H = 0 against ln Z, E and C taken directly from Kaufman's g_k:
+    two independent exact results meet through the thermodynamics code."""
+    N, NB = 144, 288
+    g = np.zeros((NB + 1, N + 1))
+    for ell, k, lg in np.loadtxt(os.path.join(GOLDEN, "square_L12_exact.txt")):
+        g[int(k), int(ell)] = g[int(k), N - int(ell)] = math.exp(lg)
+    offs, lng = oracle.exact_surface(g)
+    T = np.array([1.0, 2.0, 2.269, 2.6, 5.0])
+    got = oracle.thermo(N, NB, offs, lng, T, np.array([0.0]))[:, 0, :3]
+    lgk = exact_gk.ln_gk(12)
+    k = np.nonzero(np.isfinite(lgk))[0]
+    E = -(NB - 2.0 * k)
+    for x, t in enumerate(T):
+        a = lgk[k] - E / t
+        top = a.max()
+        w = np.exp(a - top)
+        z = w.sum()
+        e1, e2 = (w * E).sum() / z, (w * E * E).sum() / z
+        ref = [(top + math.log(z)) / N, e1 / N, (e2 - e1 * e1) / (t * t * N)]
+        assert np.allclose(got[x], ref, rtol=1e-9, atol=1e-11), (t, got[x], ref)
 
 
 def test_stored_values_agree_with_the_oracle():
