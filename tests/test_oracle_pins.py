@@ -268,6 +268,39 @@ def test_wl_accuracy_square_L4(mode):
     assert errs.max() <= 0.1
 
 
+def test_tm_closed_forms_of_lines_two_and_three():
+    """Exact g(k | l = 2, 3) on the torus for L >= 5: two up spins are adjacent
+    (k = 6, N_B ways) or not (k = 8); three are a connected straight or bent
+    cluster (k = 8, 2N + 4N), an adjacent pair and a third touching neither
+    (k = 10, N_B (N - 8)), or apart (k = 12, the rest of C(N, 3))."""
+    for L in (5, 6, 8):
+        g = oracle.tm_square(L)
+        N, NB = L * L, 2 * L * L
+        assert g[6, 2] == NB and g[8, 2] == math.comb(N, 2) - NB
+        assert g[8, 3] == 6 * N and g[10, 3] == NB * (N - 8)
+        assert g[12, 3] == math.comb(N, 3) - 6 * N - NB * (N - 8)
+
+
+def test_walk_L256_lines_two_and_three_against_closed_forms():
+    """The walk on the 65536-site torus, where nothing can be enumerated: lines
+    l = 2 and 3 to ln f_min = 1e-6 visit exactly the k the closed forms allow,
+    the dominant bin (fixed by the Eq. 4 normalisation) matches to 1e-3, and the
+    rare bins are within 0.75 -- the walker reaches them ~10^-4 of the time, and
+    Wang-Landau's error on such bins stays at a few tenths whatever the stage
+    length (the end effect remarked in the discussion of Fig. 5)."""
+    L, N, NB, u = 256, 65536, 131072, 1e-6
+    exact = {2: {6: NB, 8: math.comb(N, 2) - NB},
+             3: {8: 6 * N, 10: NB * (N - 8), 12: math.comb(N, 3) - 6 * N - NB * (N - 8)}}
+    for ell, ex in exact.items():
+        st = oracle.run_line(oracle.SQUARE, L, ell, 1, u, 10**6)
+        assert st.converged and oracle.audit(st) == 0
+        lg = oracle.assemble(N, ell, st.lng, st.visited, u)
+        assert sorted(2 * np.nonzero(np.isfinite(lg))[0]) == sorted(ex)
+        top = max(ex, key=ex.get)
+        for k, n in ex.items():
+            assert abs(lg[k // 2] - math.log(n)) < (1e-3 if k == top else 0.75), (ell, k)
+
+
 # --------------------------------------------------------------------------
 # The stored exact L=12 surface (tests/golden/square_L12_exact.txt, written by
 # tests/golden/make_golden.py from the oracle's transfer matrix)
