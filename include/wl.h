@@ -89,8 +89,9 @@ size_t wl_required_bytes(wl_lattice lattice, int L);
 
 /* Set an integer option before (or between) runs.  Keys:
  *   "seed"           Philox key word 1 of every walker (default 1)
- *   "deterministic"  1: integer acceptance against the exp threshold table,
- *                    bit-identical to the reference walk; 0: FP32 exp (default 1)
+ *   "deterministic"  1: integer acceptance against the exp threshold table, the
+ *                    chain bit-identical to the same walk taken one move at a
+ *                    time (the CPU oracle's); 0: FP32 exp (default 1)
  *   "check_interval" C: flatness is tested whenever t is a multiple of C (default 1000)
  *   "move_budget"    per-line cap on the move counter t (default 2^62)
  *   "mapping"        lanes per walker S in {1,2,4,8,16,32}; 0 = autotune (default 0)
@@ -151,6 +152,7 @@ wl_status wl_get_lng(wl_handle h, int ell, double* out, size_t cap,
 wl_status wl_get_surface(wl_handle h, double* out, size_t cap, int64_t* offsets,
                          size_t offsets_cap, size_t* n_out);
 
+/* Counters and timings of the handle (wl_stats above) into *out. */
 wl_status wl_get_stats(wl_handle h, wl_stats* out);
 
 /* Thermodynamics from the assembled surface (the partition function of Eq. 2
@@ -165,7 +167,7 @@ wl_status wl_thermo(wl_handle h, const double* T, int nT, const double* H, int n
  * in units of u), stage, accepts, t at stage start, status (0 running,
  * 1 converged, 2 overflow), flatness checks}; perm[N] = up-spin list in
  * entries [0, l) followed by the down-spin list; spins[N] = 0/1 per site;
- * lng, hist, visited: one entry per bin (k = 2b).  Any pointer may be NULL. */
+ * lng, hist, visited: one entry per bin (k = b * k_step).  Any pointer may be NULL. */
 wl_status wl_get_line_state(wl_handle h, int ell, int64_t* scal, int32_t* perm,
                             uint8_t* spins, int64_t* lng, int64_t* hist, uint8_t* visited);
 
@@ -178,6 +180,7 @@ wl_status wl_get_exp_table(wl_handle h, uint64_t* table, int* q);
  * Philox(ctr[4i..4i+3], key[2i..2i+1]).  Host arrays.  For verification. */
 wl_status wl_philox(size_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out);
 
+/* Free the handle's device memory and the handle; h is invalid afterwards. */
 wl_status wl_destroy(wl_handle h);
 
 /* ---- Serving: density-of-states requests with continuous batching ----
@@ -232,8 +235,8 @@ wl_status wl_server_destroy(wl_server s);
  * Walks lines ell_first .. ell_first+nlines-1 (all <= N/2; nlines <= 4096, the
  * scratch limit -- larger requests return WL_EINVAL before any launch) of the
  * periodic lattice, exactly as wl_run does with the same options (seed,
- * deterministic, check_interval, move_budget, mapping; 0 = 8 lanes per walker),
- * on `stream` (a cudaStream_t as an integer, 0 = default stream), and returns
+ * deterministic, check_interval, move_budget, mapping; 0 = 8 lanes per walker;
+ * batches resolved as with "resolve" = 0), on `stream` (a cudaStream_t as an integer, 0 = default stream), and returns
  * when every line converged (WL_OK) or reached move_budget (WL_ENOTCONVERGED).
  * init != 0 first initialises every line (as the first wl_run does); init == 0
  * continues the state held in the buffers.  Caller-owned DEVICE buffers:
