@@ -14,6 +14,12 @@ with the CPU oracle.
 Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank walks its own
 surface (seed offset by rank): per-GPU work is fixed, scaling is weak, and the
 only cross-rank traffic is the barrier and the max-over-ranks of the timings.
+
+Other modes, each printing its own JSON line: --converge L (time to ln f_min
+of a whole surface; for square L with stored exact values also the surface
+summed over l against the exact zero-field g_k, as in Fig. 5), --serve N
+(Poisson request stream through the serving loop), --accuracy (12x12 against
+the exact surface), --L (the benchmark on another square lattice).
 """
 from __future__ import annotations
 
