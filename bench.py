@@ -188,6 +188,26 @@ def exact_gk_comparison(lng_k, path: str, NB: int):
             "worst_k": int(ks[int(np.argmax(d))])}
 
 
+def line_moves_summary(moves, N: int):
+    """Moves each line took to reach ln f_min (its move counter t), lines
+    l = 0..N/2: quantiles, a log2 histogram and the four lines the paper walks
+    individually (l = N/8, N/4, 3N/8, N/2)."""
+    import numpy as np
+    t = np.asarray(moves, dtype=np.int64)
+    walked = t[t > 0]
+    q = np.quantile(walked, [0.5, 0.9, 0.99, 1.0]) if walked.size else [0, 0, 0, 0]
+    hist = {}
+    for v in walked:
+        b = int(v).bit_length() - 1
+        hist[f"2^{b}"] = hist.get(f"2^{b}", 0) + 1
+    return {"lines_walked": int(walked.size),
+            "p50": int(q[0]), "p90": int(q[1]), "p99": int(q[2]), "max": int(q[3]),
+            "argmax_l": int(np.argmax(t)) if t.size else 0,
+            "log2_histogram": dict(sorted(hist.items(), key=lambda kv: int(kv[0][2:]))),
+            "paper_lines": {str(l): int(t[l]) for l in (N // 8, N // 4, 3 * N // 8, N // 2)
+                            if l < t.size}}
+
+
 def run_converge(args):
     """Time to ln f_min: one whole surface walked until every line converged
     (or the time limit), reported as its own JSON line."""
@@ -209,6 +229,8 @@ def run_converge(args):
             "min_stage": st["min_stage"], "max_stage": st["max_stage"], "moves": st["moves"],
             "moves_per_s": st["moves"] / sec, "mapping": st["mapping"],
             "accept_rate": st["accepts"] / max(st["moves"], 1)}
+    line["moves_to_converge"] = line_moves_summary(
+        [h.line_state(ell)["sc"][1] for ell in range(h.N // 2 + 1)], h.N)
     exact = os.path.join(ROOT, "tests", "golden", f"square_L{Lc}_gk_exact.txt")
     if lat == "square" and os.path.exists(exact):
         h.assemble()

@@ -38,3 +38,15 @@ def test_reference_arm_prints_one_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_line_moves_summary():
+    N = 64
+    t = [0, 0] + [1000 * (l + 1) for l in range(2, N // 2 + 1)]   # lines 0 and 1 never walk
+    r = bench.line_moves_summary(t, N)
+    assert r["lines_walked"] == N // 2 - 1
+    assert r["max"] == 33000 and r["argmax_l"] == N // 2
+    assert r["paper_lines"] == {"8": 9000, "16": 17000, "24": 25000, "32": 33000}
+    assert sum(r["log2_histogram"].values()) == r["lines_walked"]
+    assert r["log2_histogram"]["2^11"] == 2                        # 3000 and 4000 lie in [2048, 4096)
+    assert r["log2_histogram"]["2^14"] == 16                       # 17000 .. 32000
