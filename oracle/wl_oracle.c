@@ -10,16 +10,19 @@
  * from it.
  *
  * Contents (each function names the passage it follows):
- *   - periodic lattices: square, triangular, simple cubic  (the model, Eq. 1)
+ *   - periodic lattices: square, triangular, simple cubic  (the model, Eq. 1),
+ *     and the square lattice with open boundaries (Fig. 2)
  *   - Philox4x32-10 counter-based generator (Salmon et al., SC'11), written
  *     from its published definition; the walk's random numbers come from it
  *   - the 4096-entry fixed-point exp threshold table
  *   - one Wang-Landau walk on one micromagnetic line (Eq. 3, Eq. 4 and the
  *     surrounding text: lists, spin-exchange move, g/h update, flatness,
- *     f -> f^(1/4), stop at f_min)
+ *     f -> f^(1/4), stop at f_min), with the optional extra histogram reset
+ *     at unchanged f (the remark after Eq. 4)
  *   - assembly g_kl = C(N,l) * normalized g(k|l)  (Eq. 4, Eq. 2)
  *   - exact g_kl by brute-force enumeration (definition of g_kl, Eq. 2)
  *   - exact g_kl by a site-by-site transfer matrix, square lattice
+ *   - thermodynamics from g_kl (Eq. 2 with the energy of Eq. 1)
  *
  * Fixed-point convention: ln g is kept as an int64 count of u = ln f_min,
  * ln f = F*u with F an integer; F starts at round(1/u) (f = e initially) and
