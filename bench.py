@@ -217,6 +217,11 @@ def run_converge(args):
     h = wl.Handle(lat, Lc, deterministic=1, check_interval=args.check_interval, seed=1,
                   mapping=args.mapping, timeout_ms=int(args.time_limit * 1000),
                   same_f_resets=args.same_f_resets, resolve=args.resolve)
+    lo, hi = 0, h.N // 2
+    if args.lines:
+        lo, hi = (int(x) for x in args.lines.split(":"))
+        h.set_option("ell_min", lo)
+        h.set_option("ell_max", hi)
     t0 = time.perf_counter()
     rc = h.run(args.ln_f_min, FLATNESS, allow=(wl.WL_OK, wl.WL_ETIMEOUT))
     sec = time.perf_counter() - t0
@@ -229,10 +234,13 @@ def run_converge(args):
             "min_stage": st["min_stage"], "max_stage": st["max_stage"], "moves": st["moves"],
             "moves_per_s": st["moves"] / sec, "mapping": st["mapping"],
             "accept_rate": st["accepts"] / max(st["moves"], 1)}
-    line["moves_to_converge"] = line_moves_summary(
-        [h.line_state(ell)["sc"][1] for ell in range(h.N // 2 + 1)], h.N)
+    moves = [0] * (h.N // 2 + 1)
+    for ell in range(lo, hi + 1):
+        moves[ell] = int(h.line_state(ell)["sc"][1])
+    line["lines_walked"] = [lo, hi]
+    line["moves_to_converge"] = line_moves_summary(moves, h.N)
     exact = os.path.join(ROOT, "tests", "golden", f"square_L{Lc}_gk_exact.txt")
-    if lat == "square" and os.path.exists(exact):
+    if lat == "square" and os.path.exists(exact) and (lo, hi) == (0, h.N // 2):
         h.assemble()
         lines = [h.get_lng(ell) for ell in range(h.N // 2 + 1)]
         line["sum_over_lines_vs_exact_gk"] = exact_gk_comparison(
@@ -586,6 +594,7 @@ def main():
     ap.add_argument("--ln-f-min", type=float, default=LN_F_MIN)
     ap.add_argument("--check-interval", type=int, default=CHECK_INTERVAL)
     ap.add_argument("--time-limit", type=float, default=600.0, help="seconds, --converge only")
+    ap.add_argument("--lines", default="", help="A:B, walk only lines A..B (--converge only)")
     ap.add_argument("--same-f-resets", type=int, default=0, help="extra same-f resets per stage")
     ap.add_argument("--resolve", type=int, default=0, choices=[0, 1, 2],
                     help="batch resolution: 0 by acceptance rate, 1 single steps, 2 rounds")
