@@ -208,6 +208,30 @@ def line_moves_summary(moves, N: int):
                             if l < t.size}}
 
 
+def converge_on_cpu(lat, Lc, lo, hi, args, gpu_moves):
+    """The same surface walked to ln f_min by the oracle (deterministic, as it
+    stands) on every host core, one line per thread, largest lines first; the
+    chain is the GPU's, so each line's move count must match."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    code = oracle.LATTICE_NAMES[lat]
+    threads = os.cpu_count() or 1
+    ells = sorted(range(lo, hi + 1), key=lambda l: -oracle.line_nbins(code, Lc, l))
+
+    def one(ell):
+        st = oracle.run_line(code, Lc, ell, 1, args.ln_f_min, args.check_interval,
+                             int(FLATNESS * 1000), 2**62, 0, same_f_resets=args.same_f_resets)
+        return ell, st.t
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        res = dict(ex.map(one, ells))
+    sec = time.perf_counter() - t0
+    same = all(res[l] == gpu_moves[l] for l in ells)
+    return {"seconds": sec, "cores": threads, "kind": "oracle", "moves": int(sum(res.values())),
+            "same_moves_per_line_as_gpu": bool(same),
+            "sample": "the whole surface, every line to ln f_min, one thread per line"}
+
+
 def run_converge(args):
     """Time to ln f_min: one whole surface walked until every line converged
     (or the time limit), reported as its own JSON line."""
@@ -216,7 +240,7 @@ def run_converge(args):
     lat, Lc = args.lattice, args.converge
     h = wl.Handle(lat, Lc, deterministic=1, check_interval=args.check_interval, seed=1,
                   mapping=args.mapping, timeout_ms=int(args.time_limit * 1000),
-                  same_f_resets=args.same_f_resets, resolve=args.resolve)
+                  same_f_resets=args.same_f_resets)
     lo, hi = 0, h.N // 2
     if args.lines:
         lo, hi = (int(x) for x in args.lines.split(":"))
@@ -228,7 +252,7 @@ def run_converge(args):
     st = h.stats()
     line = {"mode": "time_to_ln_f_min", "lattice": lat, "L": Lc, "N": h.N, "lines": st["lines"],
             "ln_f_min": args.ln_f_min, "check_interval": args.check_interval,
-            "same_f_resets": args.same_f_resets, "resolve": args.resolve,
+            "same_f_resets": args.same_f_resets,
             "status": "converged" if rc == wl.WL_OK else "time limit",
             "seconds": sec, "lines_converged": st["lines_converged"],
             "min_stage": st["min_stage"], "max_stage": st["max_stage"], "moves": st["moves"],
@@ -239,6 +263,9 @@ def run_converge(args):
         moves[ell] = int(h.line_state(ell)["sc"][1])
     line["lines_walked"] = [lo, hi]
     line["moves_to_converge"] = line_moves_summary(moves, h.N)
+    if args.cpu_converge and rc == wl.WL_OK:
+        line["cpu_oracle"] = converge_on_cpu(lat, Lc, lo, hi, args, moves)
+        line["gpu_speedup_over_cpu"] = line["cpu_oracle"]["seconds"] / sec
     exact = os.path.join(ROOT, "tests", "golden", f"square_L{Lc}_gk_exact.txt")
     if lat == "square" and os.path.exists(exact) and (lo, hi) == (0, h.N // 2):
         h.assemble()
@@ -458,8 +485,7 @@ def run_ours(args):
 
     h = wl.Handle(LATTICE, L, deterministic=1, check_interval=CHECK_INTERVAL,
                   move_budget=args.moves_per_line, slice_moves=args.moves_per_line,
-                  mapping=args.mapping, form=args.form, stream=stream.cuda_stream,
-                  resolve=args.resolve)
+                  mapping=args.mapping, form=args.form, stream=stream.cuda_stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
 
     def step(seed):
@@ -596,8 +622,8 @@ def main():
     ap.add_argument("--time-limit", type=float, default=600.0, help="seconds, --converge only")
     ap.add_argument("--lines", default="", help="A:B, walk only lines A..B (--converge only)")
     ap.add_argument("--same-f-resets", type=int, default=0, help="extra same-f resets per stage")
-    ap.add_argument("--resolve", type=int, default=0, choices=[0, 1, 2],
-                    help="batch resolution: 0 by acceptance rate, 1 single steps, 2 rounds")
+    ap.add_argument("--cpu-converge", action="store_true",
+                    help="--converge: also walk the surface with the oracle on every host core")
     ap.add_argument("--serve", type=int, default=0, help="run the serving benchmark with N requests")
     ap.add_argument("--serve-moves", type=int, default=1 << 22, help="per-line move budget of a request")
     ap.add_argument("--max-active", type=int, default=8)

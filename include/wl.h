@@ -107,11 +107,6 @@ size_t wl_required_bytes(wl_lattice lattice, int L);
  *                    while ln f is kept -- the extra reset the paper remarks
  *                    after Eq. 4 speeds the walk; its trigger is not given
  *                    there, this is one choice (default 0: off)
- *   "resolve"        how a walker resolves a batch of speculative proposals:
- *                    1 steps one at a time, 2 rounds that commit every
- *                    rejection up to the next accepted step at once, 0 picks
- *                    per walker from its recent acceptance rate (default 0).
- *                    The chain is the same in all three; only speed differs.
  * Setting "seed", "deterministic", "check_interval", "same_f_resets" or the
  * line range after a run requires wl_reset().  Errors: WL_EINVAL (unknown key or bad value), WL_ESTATE. */
 wl_status wl_set_option(wl_handle h, const char* key, int64_t value);
@@ -180,6 +175,17 @@ wl_status wl_get_exp_table(wl_handle h, uint64_t* table, int* q);
  * Philox(ctr[4i..4i+3], key[2i..2i+1]).  Host arrays.  For verification. */
 wl_status wl_philox(size_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out);
 
+/* The walker's form of Eq. 3 for n random words r[i] (the third Philox word of
+ * a move attempt): out[i] = dmax, the largest ln g increase d (in units of
+ * u = ln_f_min) that the word accepts; a move with d <= dmax is accepted, every
+ * d <= 0 included.  Deterministic rule: accept iff r < T(d), T the linear
+ * interpolation of the exp threshold table (wl_get_exp_table); production
+ * rule: accept iff (r/2^8 + 1/2) 2^-24 < exp(-u d) (FP32).  Host arrays.  For
+ * verification.  Errors: WL_EINVAL, WL_EMISMATCH (device table differs from
+ * the host-built table, deterministic only), WL_ECUDA. */
+wl_status wl_accept_threshold(double ln_f_min, int deterministic, size_t n, const uint32_t* r,
+                              int64_t* out);
+
 /* Free the handle's device memory and the handle; h is invalid afterwards. */
 wl_status wl_destroy(wl_handle h);
 
@@ -227,19 +233,25 @@ wl_status wl_server_destroy(wl_server s);
  * call cudaMalloc -- while another framework owns the device's memory pool,
  * where an allocation (or the synchronisation cudaMalloc/cudaFree may imply)
  * is not allowed, or under a memory plan fixed up front -- but can own every
- * input and output buffer.  This call allocates nothing: its scratch (exp
- * tables, line descriptors, work queue, control words, run summary) is one
- * fixed ~129 KB __device__ array inside the library, held by every GPU that
- * loads it until the process exits.
+ * input and output buffer.  This call allocates no device memory: its scratch
+ * (exp tables, line descriptors, work queue, control words, run summary) is
+ * one fixed ~129 KB __device__ array inside the library, held by every GPU
+ * that loads it until the process exits; its host staging uses fixed static
+ * arrays, not the caller's stack.
  *
  * Walks lines ell_first .. ell_first+nlines-1 (all <= N/2; nlines <= 4096, the
  * scratch limit -- larger requests return WL_EINVAL before any launch) of the
  * periodic lattice, exactly as wl_run does with the same options (seed,
- * deterministic, check_interval, move_budget, mapping; 0 = 8 lanes per walker;
- * batches resolved as with "resolve" = 0), on `stream` (a cudaStream_t as an integer, 0 = default stream), and returns
- * when every line converged (WL_OK) or reached move_budget (WL_ENOTCONVERGED).
- * init != 0 first initialises every line (as the first wl_run does); init == 0
- * continues the state held in the buffers.  Caller-owned DEVICE buffers:
+ * deterministic, check_interval, move_budget, mapping; 0 = 8 lanes per walker),
+ * on `stream` (a cudaStream_t as an integer, 0 = default stream), in slices of
+ * 2^20 moves per line, and returns when every line converged (WL_OK) or
+ * reached move_budget (WL_ENOTCONVERGED).  move_budget bounds the call: there
+ * is no timeout, and move_budget = 0 makes no move and returns
+ * WL_ENOTCONVERGED.  init != 0 first initialises every line (as the first
+ * wl_run does); init == 0 continues the state held in the buffers and must
+ * repeat the initialising call's lattice, L, lines, seed, deterministic,
+ * ln_f_min, flatness and check_interval (ln_f_min is checked against the
+ * states' ln f; the others cannot be checked).  Caller-owned DEVICE buffers:
  *   perm   nlines x P list entries, P = N rounded up so a line spans a multiple
  *          of 16 bytes; uint16 entries if N <= 65536, else uint32; 16-byte aligned
  *   spins  nlines x W uint32 words, W = ceil(N/32) rounded up to a multiple of 4
@@ -248,11 +260,14 @@ wl_status wl_server_destroy(wl_server s);
  *          (k = 0, 2, ...)
  *   state  nlines x 9 int64: k, t, F, stage, accepts, t at stage start,
  *          status, checks, batches
- * The first call on a device looks up the scratch address (cudaGetSymbolAddress),
- * so make one call before any stream capture.  Every call shares the scratch
- * and resets its control words; calls whose work overlaps on the GPU (from
- * several threads or streams) race on it and must be serialised by the caller.
- * Errors as for wl_run; the message is in wl_last_error(). */
+ * The call blocks the calling thread until its stream has finished the walk
+ * (it synchronises the stream after every slice and reads a summary into host
+ * memory), so it cannot be captured into a CUDA graph.  The first call on a
+ * device looks up the scratch address (cudaGetSymbolAddress), so that first
+ * call must not run while any stream of the process is capturing.  Every call
+ * shares the scratch and resets its control words; calls whose work overlaps on
+ * the GPU (from several threads or streams) race on it and must be serialised
+ * by the caller.  Errors as for wl_run; the message is in wl_last_error(). */
 wl_status wl_walk_noalloc(wl_lattice lattice, int L, int ell_first, int nlines, uint32_t seed,
                           int deterministic, double ln_f_min, double flatness,
                           int64_t check_interval, int64_t move_budget, int mapping, int init,

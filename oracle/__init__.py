@@ -70,6 +70,7 @@ def lib():
         L.or_line_run.argtypes = [i32, i32, i32, u32, dbl, i64, i32, i64, i32, i32, i32,
                                   vp, vp, vp, vp, vp, vp]
         L.or_line_audit.argtypes = [i32, i32, i32, vp, vp, i64]
+        L.or_flatness.argtypes = [vp, vp, i64, i32]
         L.or_assemble.argtypes = [i32, i32, i64, vp, vp, dbl, vp]
         L.or_assemble.restype = None
         L.or_brute_force.argtypes = [i32, i32, vp]
@@ -177,6 +178,15 @@ def run_line(lattice: int, L: int, ell: int, seed: int, u: float, C: int,
     if rc:
         raise ValueError("or_line_run rejected its arguments")
     return state
+
+
+def is_flat(hist, visited, flat_pm: int = 800) -> bool:
+    """The flatness test of the WL recap (80%/80% at flat_pm = 800) on a
+    histogram over a line's bins; only visited bins take part."""
+    h = np.ascontiguousarray(hist, dtype=np.int64)
+    v = np.ascontiguousarray(visited, dtype=np.uint8)
+    assert h.shape == v.shape
+    return bool(lib().or_flatness(_p(h), _p(v), h.size, flat_pm))
 
 
 def audit(state: LineState) -> int:

@@ -353,6 +353,12 @@ static int or_is_flat(const int64_t* hist, const uint8_t* visited, int64_t nbins
     return 1000 * c >= (int64_t)flat_pm * n;
 }
 
+/* Exported for the tests: the flatness test on a given histogram. */
+int or_flatness(const int64_t* hist, const uint8_t* visited, int64_t nbins, int flat_pm)
+{
+    return or_is_flat(hist, visited, nbins, flat_pm);
+}
+
 /* Run the walk on line ell until F == 0 (converged) or t == budget.
  *   mode 0: deterministic -- acceptance r2 < T(d) against the exp table
  *   mode 1: production   -- acceptance U53(r2, r3) < exp(-u d) in double

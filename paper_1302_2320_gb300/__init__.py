@@ -8,7 +8,7 @@ kernels.  There is no CPU fallback: if the library is missing or fails to load,
 
 The C names are kept: ``wl_create``, ``wl_set_option``, ``wl_run``,
 ``wl_assemble``, ``wl_get_lng``, ``wl_get_surface``, ``wl_get_stats``,
-``wl_get_line_state``, ``wl_get_exp_table``, ``wl_philox``, ``wl_reset``,
+``wl_get_line_state``, ``wl_get_exp_table``, ``wl_philox``, ``wl_accept_threshold``, ``wl_reset``,
 ``wl_abort``, ``wl_destroy``, ``wl_last_error``.  ``Handle`` wraps a handle
 with the same calls as methods.
 """
@@ -33,7 +33,7 @@ WL_OK, WL_ENOTCONVERGED, WL_ETIMEOUT, WL_EABORTED = 0, 6, 4, 5
 
 EXPORTED = ["wl_create", "wl_required_bytes", "wl_set_option", "wl_get_option", "wl_run",
             "wl_abort", "wl_reset", "wl_assemble", "wl_get_lng", "wl_get_surface",
-            "wl_get_stats", "wl_get_line_state", "wl_get_exp_table", "wl_philox", "wl_destroy",
+            "wl_get_stats", "wl_get_line_state", "wl_get_exp_table", "wl_philox", "wl_accept_threshold", "wl_destroy",
             "wl_last_error", "wl_walk_noalloc", "wl_server_create", "wl_server_submit",
             "wl_server_info", "wl_server_wait", "wl_server_result", "wl_server_release",
             "wl_server_destroy", "wl_thermo"]
@@ -96,6 +96,7 @@ def lib():
         L.wl_get_line_state.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
         L.wl_get_exp_table.argtypes = [vp, vp, vp]
         L.wl_philox.argtypes = [sz, vp, vp, vp]
+        L.wl_accept_threshold.argtypes = [dbl, i32, sz, vp, vp]
         L.wl_destroy.argtypes = [vp]
         L.wl_last_error.argtypes = []
         L.wl_last_error.restype = cp
@@ -136,6 +137,16 @@ def wl_philox(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:
     key = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
     out = np.zeros_like(ctr)
     _check(lib().wl_philox(ctr.shape[0], _p(ctr), _p(key), _p(out)), "wl_philox")
+    return out
+
+
+def wl_accept_threshold(ln_f_min: float, deterministic: int, r: np.ndarray) -> np.ndarray:
+    """dmax of Eq. 3 for each random word: a move with ln g increase d (units of
+    ln_f_min) is accepted iff d <= dmax."""
+    r = np.ascontiguousarray(r, dtype=np.uint32).ravel()
+    out = np.zeros(r.size, dtype=np.int64)
+    _check(lib().wl_accept_threshold(ln_f_min, int(deterministic), r.size, _p(r), _p(out)),
+           "wl_accept_threshold")
     return out
 
 

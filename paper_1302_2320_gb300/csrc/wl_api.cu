@@ -125,22 +125,12 @@ size_t required_bytes(const LatInfo& g, const Layout& lo)
 
 // Host-side exp threshold table, an independent evaluation in long double used
 // to verify the device-built table bit for bit before a deterministic run.
-int host_table_q(double u)
-{
-    const double need = 32.0 * std::log(2.0);
-    for (int q = 0; q < 40; ++q)
-        if (4095.0 * std::ldexp(1.0, q) * u >= need) return q;
-    return -1;
-}
+int host_table_q(double u) { return wl::rt::table_shift(u); }
 
 void host_table(double u, int q, std::vector<uint64_t>& t)
 {
     t.resize(kTableN);
-    for (int i = 0; i < kTableN; ++i) {
-        volatile double x = (double)((uint64_t)i << q) * u;
-        long double v = std::ldexp(std::exp(-(long double)x), 32) + 0.5L;
-        t[i] = (uint64_t)std::floor(v);
-    }
+    for (int i = 0; i < kTableN; ++i) t[i] = wl::rt::table_entry(u, q, i);
 }
 
 struct TuneKey {
@@ -347,12 +337,12 @@ WalkArgs base_args(wl_ctx* h)
     a.qnext = h->d_qheads + h->lo.nlines;
     a.nqueue = h->nqueue;
     a.q = h->q;
-    a.neg_u_log2e = (float)(-h->u * 1.4426950408889634);
+    a.seg_per_log2 = (float)(std::log(2.0) / (std::ldexp(1.0, h->q) * h->u));
+    a.inv_u = (float)(1.0 / h->u);
     a.seed = h->seed;
     a.flat_pm = h->flat_pm;
     a.pstride = h->lo.pstride;
     a.same_f_resets = h->same_f_resets;
-    a.resolve = h->resolve;
     a.C = h->C;
     a.budget = h->budget;
     a.slice_moves = h->slice_moves;
@@ -368,7 +358,7 @@ wl_status persistent_shape(wl_ctx* h, int S, int* blocks_per_sm_out, Shape* sh)
 {
     const size_t isz = h->lo.idx16 ? 2 : 4;
     const size_t stg = (size_t)h->lo.pstride * isz + (size_t)h->lo.W * 4;
-    const size_t cap = std::min<size_t>(h->max_smem, 220 * 1024) - kTableBytes;
+    const size_t cap = std::min<size_t>(h->max_smem, 220 * 1024);
     const int groups_per_warp = 32 / S;
     int stage = 0, max_warps = 0;
     size_t slot = kWinBytes;
@@ -387,7 +377,7 @@ wl_status persistent_shape(wl_ctx* h, int S, int* blocks_per_sm_out, Shape* sh)
     long best_cap = -1;
     for (int w = 1; w <= max_warps; ++w) {
         const int threads = w * 32;
-        const size_t smem = kTableBytes + (size_t)(threads / S) * slot;
+        const size_t smem = (size_t)(threads / S) * slot;
         int bps = 0;
         CU(walk_kernel_attrs(kernel_lattice(h), S, h->det != 0, h->lo.idx16, smem, threads, &bps));
         if (bps < 1) continue;
@@ -406,7 +396,7 @@ wl_status persistent_shape(wl_ctx* h, int S, int* blocks_per_sm_out, Shape* sh)
     }
     if (best_w == 0) return fail(WL_ECUDA, "walker kernel cannot be resident (S=%d)", S);
     const int threads = best_w * 32;
-    const size_t smem = kTableBytes + (size_t)(threads / S) * slot;
+    const size_t smem = (size_t)(threads / S) * slot;
     const int groups_per_block = threads / S;
     const int need_blocks = (h->nqueue + groups_per_block - 1) / groups_per_block;
     const int blocks = std::max(1, std::min(need_blocks, h->num_sms * best_bps));
@@ -595,10 +585,10 @@ wl_status run_plain(wl_ctx* h)
     }
     const size_t isz = h->lo.idx16 ? 2 : 4;
     const size_t stg = (size_t)h->lo.pstride * isz + (size_t)h->lo.W * 4;
-    const int stage = (kTableBytes + kWinBytes + stg <= std::min<size_t>(h->max_smem, 220 * 1024) &&
+    const int stage = (kWinBytes + stg <= std::min<size_t>(h->max_smem, 220 * 1024) &&
                        stg <= 64 * 1024) ? 1 : 0;
     const size_t slot = kWinBytes + (stage ? stg : 0);
-    const size_t smem = kTableBytes + slot;
+    const size_t smem = slot;
     CU(cudaMemsetAsync(h->d_qheads, 0, h->lo.nlines * 4, h->s));
     CU(cudaEventRecord(h->ev_join, h->s));
     for (auto st : h->pool) CU(cudaStreamWaitEvent(st, h->ev_join, 0));
@@ -690,6 +680,21 @@ wl_status summary_status(wl_ctx* h, const Summary& sm) { return check_flags(h, s
 
 size_t handle_bytes(const wl_ctx* h) { return required_bytes(h->g, h->lo); }
 
+int table_shift(double u)
+{
+    const double need = 32.0 * std::log(2.0);
+    for (int q = 0; q < 40; ++q)
+        if (4095.0 * std::ldexp(1.0, q) * u >= need) return q;
+    return -1;
+}
+
+uint64_t table_entry(double u, int q, int i)
+{
+    volatile double x = (double)((uint64_t)i << q) * u;
+    const long double v = std::ldexp(std::exp(-(long double)x), 32) + 0.5L;
+    return (uint64_t)std::floor(v);
+}
+
 }  // namespace rt
 }  // namespace wl
 
@@ -772,9 +777,6 @@ wl_status wl_set_option(wl_handle h, const char* key, int64_t v)
     } else if (k == "same_f_resets") {
         if (v < 0 || v > 1000000) return fail(WL_EINVAL, "same_f_resets must be in [0, 10^6]");
         h->same_f_resets = (int)v;
-    } else if (k == "resolve") {
-        if (v < 0 || v > 2) return fail(WL_EINVAL, "resolve must be 0, 1 or 2");
-        h->resolve = (int)v;
     } else if (k == "ell_min" || k == "ell_max") {
         if (v < 0 || v >= h->lo.nlines) return fail(WL_EINVAL, "%s must be in [0, %d]", key, h->lo.nlines - 1);
         (k == "ell_min" ? h->ell_min : h->ell_max) = (int)v;
@@ -800,7 +802,6 @@ wl_status wl_get_option(wl_handle h, const char* key, int64_t* v)
     else if (k == "hbm_budget") *v = h->hbm_budget;
     else if (k == "ell_min") *v = h->ell_min;
     else if (k == "same_f_resets") *v = h->same_f_resets;
-    else if (k == "resolve") *v = h->resolve;
     else if (k == "ell_max") *v = h->ell_max;
     else if (k == "N") *v = h->g.N;
     else if (k == "NB") *v = h->g.NB;
@@ -1028,6 +1029,47 @@ wl_status wl_get_exp_table(wl_handle h, uint64_t* table, int* q)
     if (!h->initialized || h->table64.empty()) return fail(WL_ESTATE, "no table before the first run");
     if (table) memcpy(table, h->table64.data(), kTableN * 8);
     if (q) *q = h->q;
+    return WL_OK;
+}
+
+wl_status wl_accept_threshold(double ln_f_min, int deterministic, size_t n, const uint32_t* r,
+                              int64_t* out)
+{
+    if (!(ln_f_min >= 1e-10 && ln_f_min <= 0.5)) return fail(WL_EINVAL, "ln_f_min must be in [1e-10, 0.5]");
+    if (n == 0) return WL_OK;
+    if (!r || !out) return fail(WL_EINVAL, "NULL argument");
+    const int q = host_table_q(ln_f_min);
+    uint64_t* d64 = nullptr;
+    uint32_t *d32 = nullptr, *dr = nullptr;
+    int64_t* dout = nullptr;
+    std::vector<uint64_t> t64(kTableN), ref;
+    std::vector<uint32_t> t32(kTableN);
+    host_table(ln_f_min, q, ref);
+    cudaError_t e = cudaMalloc(&d64, kTableN * 8);
+    if (!e) e = cudaMalloc(&d32, kTableN * 4);
+    if (!e) e = cudaMalloc(&dr, n * 4);
+    if (!e) e = cudaMalloc(&dout, n * 8);
+    if (!e) e = launch_exp_table(ln_f_min, q, d64, 0);
+    if (!e) e = cudaMemcpy(t64.data(), d64, kTableN * 8, cudaMemcpyDeviceToHost);
+    bool same = true;
+    if (!e) {
+        for (int i = 0; i < kTableN; ++i) same &= t64[i] == ref[i];
+        t32[0] = 0xFFFFFFFFu;
+        for (int i = 1; i < kTableN; ++i) t32[i] = (uint32_t)t64[i];
+        e = cudaMemcpy(d32, t32.data(), kTableN * 4, cudaMemcpyHostToDevice);
+    }
+    if (!e) e = cudaMemcpy(dr, r, n * 4, cudaMemcpyHostToDevice);
+    if (!e)
+        e = launch_dmax(n, dr, deterministic ? 1 : 0, d32, q,
+                        (float)(std::log(2.0) / (std::ldexp(1.0, q) * ln_f_min)),
+                        (float)(1.0 / ln_f_min), dout, 0);
+    if (!e) e = cudaMemcpy(out, dout, n * 8, cudaMemcpyDeviceToHost);
+    cudaFree(d64);
+    cudaFree(d32);
+    cudaFree(dr);
+    cudaFree(dout);
+    if (e) return fail(WL_ECUDA, "wl_accept_threshold: %s", cudaGetErrorString(e));
+    if (deterministic && !same) return fail(WL_EMISMATCH, "device exp table differs from the host table");
     return WL_OK;
 }
 

@@ -1,7 +1,7 @@
 // wl_device.cuh -- device building blocks of the micromagnetic-line
 // Wang-Landau walker (arXiv:1302.2320): Philox4x32-10, lattice geometry on
-// bit-packed spins, the change of k under a spin exchange, the fixed-point
-// acceptance of Eq. 3, and warp-group helpers.
+// bit-packed spins, the change of k under a spin exchange, the acceptance of
+// Eq. 3 as a threshold on the ln g difference, and warp-group helpers.
 #pragma once
 
 #include <cstdint>
@@ -64,14 +64,14 @@ struct WalkArgs {
     int32_t* qnext;          // work queue head
     int32_t nqueue;
     int32_t q;               // table shift
-    float neg_u_log2e;       // -u * log2(e), production acceptance
+    float seg_per_log2;      // ln 2 / (2^q u): table segments per halving of exp(-u d)
+    float inv_u;             // 1 / u, production acceptance
     uint32_t seed;
     int32_t flat_pm;         // flatness fraction x in 1/1000
     int32_t stage_smem;      // 1: lists and spins staged in shared memory
     int32_t slot_bytes;      // shared bytes per walker slot (window + staged list/spins)
     int32_t pstride;         // list entries per line, N rounded up to 16 bytes
     int32_t same_f_resets;   // R > 0: extra histogram resets at unchanged f (see walk_line)
-    int32_t resolve;         // batch resolution: 0 by acceptance rate, 1 single steps, 2 rounds
     int64_t C;               // flatness check interval
     int64_t budget;          // per-line cap on t
     int64_t slice_moves;     // moves per line in this launch
@@ -171,29 +171,6 @@ __device__ __forceinline__ unsigned open_neighbours(const Geo& g, uint32_t i, ui
     return v;
 }
 
-// Change of k when up-spin i and down-spin j are exchanged.  With u_i, u_j the
-// up neighbours of i and j in the current configuration and a_ij the number
-// of bonds between them, each bond (i, m), m != j, turns from unhappy to happy
-// or back according to s_m, giving 2u_i - z; the bonds of j give -(2u_j - z);
-// the i-j bond stays unhappy but was counted -1 on each side, so
-//     dk = 2 (u_i - u_j + a_ij).
-template <int LAT>
-__device__ __forceinline__ int delta_k(const Geo& g, const uint32_t* sp, uint32_t i, uint32_t j)
-{
-    constexpr int z = Coord<LAT>::z;
-    uint32_t ni[z], nj[z];
-    neighbours<LAT>(g, i, ni);
-    neighbours<LAT>(g, j, nj);
-    int ui = 0, uj = 0, a = 0;
-#pragma unroll
-    for (int m = 0; m < z; ++m) {
-        ui += (int)spin_at(sp, ni[m]);
-        uj += (int)spin_at(sp, nj[m]);
-        a += (int)(ni[m] == j);
-    }
-    return 2 * (ui - uj + a);
-}
-
 // delta_k that also returns the neighbour lists of i and j (used to decide
 // which later proposals an accepted exchange of i and j can affect).
 template <int LAT>
@@ -227,31 +204,75 @@ __device__ __forceinline__ int delta_k_nb(const Geo& g, const uint32_t* sp, uint
     return 2 * (ui - uj + a);
 }
 
-// Eq. 3 for an uphill move of d > 0 units of u.
-//  deterministic: accept iff r < T(d), T linearly interpolated in the table
-//  production:    accept iff U24(r) < 2^(-d u log2 e) in FP32
-template <bool DET>
-__device__ __forceinline__ bool accept_uphill(int64_t d, uint32_t r, const uint32_t* tab, int q,
-                                              float neg_u_log2e)
+// Eq. 3 as a threshold on d, the ln g difference g(k')/g(k) in units of u.
+// Both acceptance rules are non-increasing in d, so the uphill moves a random
+// word r accepts are d = 1 .. dmax(r), and a move is accepted iff d <= dmax(r)
+// (every d <= 0 is accepted: dmax >= 0).  dmax depends on the random word
+// only, so it is computed when the word is drawn, ahead of the walk.
+//
+// Deterministic rule: accept iff r < T(d), T the linear interpolation of the
+// 4096-entry table t[i] = round(2^32 exp(-i 2^q u)) (t[0] = 2^32 implicit,
+// T = 0 from d = 4095 * 2^q on).  With i* the last segment whose left entry is
+// above r, the accepted d of that segment are those with
+//     (t0 - t1) * frac >> q  <  t0 - r,
+// a bound on frac solved exactly in integers below.  i* is first estimated
+// from the exponential form of the table and then confirmed (or walked to)
+// by integer comparisons, so the result never depends on the estimate.
+__device__ __forceinline__ uint64_t table_at(const uint32_t* tab, int i)
 {
-    if (DET) {
-        // branch-free: d <= 0 or past the table gives an index that is clamped
-        // (the caller ignores the result for d <= 0)
-        const uint64_t iu = (uint64_t)d >> q;
-        const bool in = d > 0 && iu < (uint64_t)(kTableN - 1);
-        const uint32_t i = in ? (uint32_t)iu : 0u;
-        // t0 - t1 < 2^32 and the fraction < 2^q <= 2^30: one 32x32->64 product
-        const uint32_t t1 = tab[i + 1];
-        const uint64_t t0 = i == 0 ? (1ull << 32) : (uint64_t)tab[i];
-        const uint32_t diff = (uint32_t)(t0 - t1);
-        const uint32_t fr = (uint32_t)d & ((1u << q) - 1u);
-        const uint64_t T = t0 - (((uint64_t)diff * fr) >> q);
-        return in && (uint64_t)r < T;
-    } else {
-        const float p = exp2f((float)d * neg_u_log2e);
-        return (float)(r >> 8) * 0x1p-24f < p;
-    }
+    return i == 0 ? (1ull << 32) : (uint64_t)__ldg(tab + i);
 }
+
+__device__ __forceinline__ int64_t dmax_det(uint32_t r, const uint32_t* tab, int q, float seg_per_log2)
+{
+    // t[i] ~ 2^32 * 2^(-i / seg_per_log2)  =>  i ~ (32 - log2 r) * seg_per_log2
+    int c = __float2int_rd((32.0f - __log2f((float)r + 0.5f)) * seg_per_log2);
+    c = c < 0 ? 0 : (c > kTableN - 2 ? kTableN - 2 : c);
+    uint64_t t0 = table_at(tab, c), t1 = table_at(tab, c + 1);
+    // i* = max{i <= 4094 : t[i] > r}; t is non-increasing
+    while (t0 <= (uint64_t)r) {               // too far right (c > 0 here: t[0] > r)
+        --c;
+        t1 = t0;
+        t0 = table_at(tab, c);
+    }
+    while (c < kTableN - 2 && t1 > (uint64_t)r) {   // too far left
+        ++c;
+        t0 = t1;
+        t1 = table_at(tab, c + 1);
+    }
+    if (t1 > (uint64_t)r) return ((int64_t)(kTableN - 1) << q) - 1;   // whole last segment
+    // largest frac < 2^q with diff * frac < X 2^q, i.e. floor((X 2^q - 1) / diff)
+    const uint64_t X = t0 - (uint64_t)r;          // 1 .. diff
+    const uint64_t diff = t0 - t1;
+    const uint64_t num = (X << q) - 1ull;
+    const float rd = __frcp_rn((float)diff);
+    int64_t fr = (int64_t)((float)num * rd);
+    // one refinement of the float quotient by its integer residual, then exact steps
+    fr += (int64_t)((float)((int64_t)num - (int64_t)(diff * (uint64_t)fr)) * rd);
+    if (fr < 0) fr = 0;
+    while (fr > 0 && diff * (uint64_t)fr > num) --fr;
+    while (diff * (uint64_t)(fr + 1) <= num) ++fr;
+    return ((int64_t)c << q) + fr;
+}
+
+// Production rule: accept iff U < exp(-u d), U = (r/2^8 + 1/2) 2^-24 in (0, 1),
+// i.e. d < -ln(U) / u; dmax = floor of that bound (FP32).  Near U = 1 the
+// logarithm is taken of 1 - U, which is exact in FP32 there.
+__device__ __forceinline__ int64_t dmax_prod(uint32_t r, float inv_u)
+{
+    const uint32_t mm = r >> 8;
+    const float nl = mm >= (1u << 23) ? -log1pf(-((float)((1u << 24) - mm) - 0.5f) * 0x1p-24f)
+                                      : -__logf(((float)mm + 0.5f) * 0x1p-24f);
+    const float bound = nl * inv_u;
+    return bound >= 0x1p62f ? ((int64_t)1 << 62) : (int64_t)bound;
+}
+
+// The random numbers of one move attempt, drawn ahead of the walk: list slots
+// a (of the l up spins) and b (of the N - l down spins) and dmax of Eq. 3.
+struct Draw {
+    uint32_t a, b;
+    int64_t dmax;
+};
 
 // ---------------------------------------------------------------------------
 // Group helpers: S consecutive lanes of a warp serve one walker.

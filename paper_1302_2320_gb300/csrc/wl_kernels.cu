@@ -281,6 +281,24 @@ cudaError_t launch_philox(size_t n, const uint32_t* ctr, const uint32_t* key, ui
     return cudaGetLastError();
 }
 
+// dmax of Eq. 3 (the walker's acceptance threshold on d) for n random words.
+__global__ void dmax_kernel(size_t n, const uint32_t* r, int det, const uint32_t* tab, int q,
+                            float seg_per_log2, float inv_u, int64_t* out)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = det ? dmax_det(r[i], tab, q, seg_per_log2) : dmax_prod(r[i], inv_u);
+}
+
+cudaError_t launch_dmax(size_t n, const uint32_t* r, int det, const uint32_t* tab, int q,
+                        float seg_per_log2, float inv_u, int64_t* out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    clear_stale_error();
+    dmax_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, r, det, tab, q, seg_per_log2, inv_u, out);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Run summary after each walker launch: one block reduces the line states.
 // ---------------------------------------------------------------------------

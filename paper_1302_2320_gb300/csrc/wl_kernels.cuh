@@ -58,6 +58,8 @@ cudaError_t launch_assemble(const LineDesc* desc, const int64_t* lng, const hist
 cudaError_t launch_exp_table(double u, int q, uint64_t* out, cudaStream_t s);
 cudaError_t launch_philox(size_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,
                           cudaStream_t s);
+cudaError_t launch_dmax(size_t n, const uint32_t* r, int det, const uint32_t* tab, int q,
+                        float seg_per_log2, float inv_u, int64_t* out, cudaStream_t s);
 cudaError_t launch_summary(const LineState* st, int nlines, int64_t budget, const int32_t* flags,
                            Summary* out, cudaStream_t s);
 cudaError_t launch_set_deadline(uint64_t* deadline, uint64_t timeout_ns, cudaStream_t s);

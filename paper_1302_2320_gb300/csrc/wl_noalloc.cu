@@ -21,10 +21,7 @@
 
 #include "../../include/wl.h"
 #include "wl_kernels.cuh"
-
-namespace wl {
-void set_last_error(const char* msg);   // wl_api.cu: the message wl_last_error() returns
-}
+#include "wl_runtime.cuh"
 
 using namespace wl;
 
@@ -83,13 +80,16 @@ wl_status scratch_for_current_device(unsigned char** out)
     return WL_OK;
 }
 
-int noalloc_q(double u)
-{
-    const double need = 32.0 * std::log(2.0);
-    for (int q = 0; q < 40; ++q)
-        if (4095.0 * std::ldexp(1.0, q) * u >= need) return q;
-    return -1;
-}
+// Host staging of one call (descriptors, work queue, exp tables, a copy of the
+// caller's line states), kept out of the calling thread's stack: callers on
+// small stacks (worker threads of another runtime, embedded hosts) stay safe.
+// Calls serialise their staging on g_stage_mu.
+std::mutex g_stage_mu;
+LineDesc g_desc[kNoallocMaxLines];
+int32_t g_order[kNoallocMaxLines];
+uint64_t g_t64[kTableN];
+uint32_t g_t32[kTableN];
+LineState g_state[kNoallocMaxLines];
 
 }  // namespace
 
@@ -126,7 +126,7 @@ extern "C" wl_status wl_walk_noalloc(wl_lattice lattice, int L, int ell_first, i
     if (((uintptr_t)perm | (uintptr_t)spins) & 15u) return nfail(WL_EINVAL, "perm and spins must be 16-byte aligned");
     if (((uintptr_t)lng | (uintptr_t)state | (uintptr_t)hist) & 7u)
         return nfail(WL_EINVAL, "lng, hist and state must be 8-byte aligned");
-    const int q = noalloc_q(ln_f_min);
+    const int q = wl::rt::table_shift(ln_f_min);
     if (q < 0) return nfail(WL_EINVAL, "ln_f_min out of range");
     const cudaStream_t s = (cudaStream_t)(intptr_t)stream;
     const bool idx16 = N <= 65536;
@@ -152,43 +152,56 @@ extern "C" wl_status wl_walk_noalloc(wl_lattice lattice, int L, int ell_first, i
         if (e_ != cudaSuccess) return nfail(WL_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
-    // ---- descriptors and work queue (host stack -> scratch) ----
-    LineDesc desc[kNoallocMaxLines];
-    int32_t order[kNoallocMaxLines];
+    std::unique_lock<std::mutex> stage_lock(g_stage_mu);
+    // ---- a continued walk must use the ln_f_min it was initialised with:
+    // every running line has F = F0 >> 2 stage, every converged line F = 0 ----
+    if (!init) {
+        NCU(cudaMemcpyAsync(g_state, state, (size_t)nlines * sizeof(LineState), cudaMemcpyDeviceToHost, s));
+        NCU(cudaStreamSynchronize(s));
+        const int64_t F0 = std::llround(1.0 / ln_f_min);
+        for (int i = 0; i < nlines; ++i) {
+            const LineState& ls = g_state[i];
+            const bool ok = ls.status == 1 ? ls.F == 0
+                                           : (ls.stage >= 0 && ls.stage < 32 && ls.F == (F0 >> (2 * ls.stage)));
+            if (!ok)
+                return nfail(WL_EINVAL, "line %d: state (F %lld, stage %lld) was not initialised with ln_f_min %g",
+                             ell_first + i, (long long)ls.F, (long long)ls.stage, ln_f_min);
+        }
+    }
+
+    // ---- descriptors and work queue (static host staging -> scratch) ----
     int64_t off = 0;
     for (int i = 0; i < nlines; ++i) {
         const int l = ell_first + i;
         const int lm = std::min(l, N - l);
         const int64_t khi = std::min<int64_t>((int64_t)z * lm, NB);
-        desc[i].bin_off = off;
-        desc[i].ell = l;
-        desc[i].nbins = (int)(khi / 2 + 1);
-        off += desc[i].nbins;
-        order[i] = i;
+        g_desc[i].bin_off = off;
+        g_desc[i].ell = l;
+        g_desc[i].nbins = (int)(khi / 2 + 1);
+        off += g_desc[i].nbins;
+        g_order[i] = i;
     }
-    std::stable_sort(order, order + nlines, [&](int a, int b) { return desc[a].nbins > desc[b].nbins; });
-    NCU(cudaMemcpyAsync(d_desc, desc, nlines * sizeof(LineDesc), cudaMemcpyHostToDevice, s));
-    NCU(cudaMemcpyAsync(d_order, order, nlines * 4, cudaMemcpyHostToDevice, s));
+    std::stable_sort(g_order, g_order + nlines,
+                     [&](int a, int b) { return g_desc[a].nbins > g_desc[b].nbins; });
+    NCU(cudaMemcpyAsync(d_desc, g_desc, nlines * sizeof(LineDesc), cudaMemcpyHostToDevice, s));
+    NCU(cudaMemcpyAsync(d_order, g_order, nlines * 4, cudaMemcpyHostToDevice, s));
     // control words start at zero on every call
     NCU(cudaMemsetAsync(scr + kOffCtrl, 0, 256, s));
 
     // ---- exp threshold table: built on the device, checked against the host ----
     NCU(launch_exp_table(ln_f_min, q, d_t64, s));
-    uint64_t t64[kTableN];
-    uint32_t t32[kTableN];
-    NCU(cudaMemcpyAsync(t64, d_t64, sizeof t64, cudaMemcpyDeviceToHost, s));
+    NCU(cudaMemcpyAsync(g_t64, d_t64, sizeof g_t64, cudaMemcpyDeviceToHost, s));
     NCU(cudaStreamSynchronize(s));
     if (deterministic) {
-        for (int i = 0; i < kTableN; ++i) {
-            volatile double x = (double)((uint64_t)i << q) * ln_f_min;
-            const long double v = std::ldexp(std::exp(-(long double)x), 32) + 0.5L;
-            if ((uint64_t)std::floor(v) != t64[i])
+        for (int i = 0; i < kTableN; ++i)
+            if (wl::rt::table_entry(ln_f_min, q, i) != g_t64[i])
                 return nfail(WL_EMISMATCH, "exp table entry %d differs between device and host", i);
-        }
     }
-    t32[0] = 0xFFFFFFFFu;
-    for (int i = 1; i < kTableN; ++i) t32[i] = (uint32_t)t64[i];
-    NCU(cudaMemcpyAsync(d_t32, t32, sizeof t32, cudaMemcpyHostToDevice, s));
+    g_t32[0] = 0xFFFFFFFFu;
+    for (int i = 1; i < kTableN; ++i) g_t32[i] = (uint32_t)g_t64[i];
+    NCU(cudaMemcpyAsync(d_t32, g_t32, sizeof g_t32, cudaMemcpyHostToDevice, s));
+    // pageable host -> device copies have taken the data once they return
+    stage_lock.unlock();
 
     Geo g;
     g.type = (int)lattice;
@@ -228,10 +241,10 @@ extern "C" wl_status wl_walk_noalloc(wl_lattice lattice, int L, int ell_first, i
     const int S = mapping;
     const int groups = 32 / S;
     const size_t stg = (size_t)pstride * isz + (size_t)W * 4;
-    const size_t cap = std::min<size_t>((size_t)smem_optin, 220 * 1024) - kTableBytes;
+    const size_t cap = std::min<size_t>((size_t)smem_optin, 220 * 1024);
     const int stage = ((size_t)groups * (kWinBytes + stg) <= cap && stg <= 64 * 1024) ? 1 : 0;
     const size_t slot = kWinBytes + (stage ? stg : 0);
-    const size_t smem = kTableBytes + (size_t)groups * slot;
+    const size_t smem = (size_t)groups * slot;
     int bps = 0;
     NCU(walk_kernel_attrs(klat, S, deterministic != 0, idx16, smem, 32, &bps));
     if (bps < 1) return nfail(WL_ECUDA, "walker cannot be resident");
@@ -250,7 +263,8 @@ extern "C" wl_status wl_walk_noalloc(wl_lattice lattice, int L, int ell_first, i
     a.qnext = d_qnext;
     a.nqueue = nlines;
     a.q = q;
-    a.neg_u_log2e = (float)(-ln_f_min * 1.4426950408889634);
+    a.seg_per_log2 = (float)(std::log(2.0) / (std::ldexp(1.0, q) * ln_f_min));
+    a.inv_u = (float)(1.0 / ln_f_min);
     a.seed = seed;
     a.flat_pm = flat_pm;
     a.stage_smem = stage;

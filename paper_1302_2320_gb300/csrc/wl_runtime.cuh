@@ -53,7 +53,6 @@ struct wl_ctx {
     int64_t hbm_budget = 0;
     int ell_min = 0, ell_max = 0;
     int same_f_resets = 0;
-    int resolve = 0;
     // state
     bool allocated = false, initialized = false, assembled = false;
     double u = 0.0;
@@ -114,6 +113,11 @@ wl_status launch_slice_async(wl_ctx* h, int S, const Shape& sh);
 wl_status summary_status(wl_ctx* h, const Summary& sm);
 // Device bytes held by a handle of this lattice.
 size_t handle_bytes(const wl_ctx* h);
+// The exp threshold table as built on the host, to check the device-built one:
+// q, the smallest shift with 4095 * 2^q * u >= 32 ln 2 (-1 if none below 40),
+// and entry i, round(2^32 exp(-(i 2^q) u)) evaluated in long double.
+int table_shift(double u);
+uint64_t table_entry(double u, int q, int i);
 
 }  // namespace rt
 }  // namespace wl

@@ -3,30 +3,33 @@
 //
 // One walker = one line l = S consecutive lanes of a warp ("group").  A batch
 // covers the steps t .. t+S-1:
-//   parallel phase -- lane m draws Philox(ctr = t+m) and evaluates its
-//     exchange proposal against the state at the start of the batch: list
-//     slots a, b, sites i = U[a], j = D[b], their neighbours and the change of
-//     k (all of this is independent of the acceptance decisions);
-//   resolution -- the group resolves the steps in order with Eq. 3 against
-//     the current k and ln g (every lane holds the same walker state), either
-//     one step at a time, or in rounds: while the walker stays in its bin,
-//     step m sees the ln g of step e0 plus F for each step in between, so all
-//     lanes test their own step at once, a ballot finds the first accepted
-//     step, the rejections before it are committed together, and the lanes
-//     are re-tested only when an accepted step changes the bin.  Each walker
-//     takes rounds while fewer than half of its recent steps were accepted.
-//     An accepted exchange of (i_s, j_s) leaves a later proposal exact unless
-//     it reuses list slot a_s or b_s or has i_s or j_s among its sites'
-//     neighbours; such proposals are marked, and the batch ends at the first
-//     marked one (or when a proposal's bin leaves the ln g window).
-// The accepted exchanges of a batch are mutually independent and are applied
-// together after the resolution.  Random numbers are keyed by t, so the committed
-// chain is the sequential chain, bit for bit, for every S.  Batches never cross
-// a flatness check (t multiple of C) or the end of the slice.
+//   draw -- lane m holds the random numbers of step t+m, drawn one batch
+//     ahead: the list slots a, b and dmax, the largest ln g increase that
+//     Eq. 3 accepts with this step's random word (see dmax_det / dmax_prod);
+//   propose -- lane m evaluates its exchange against the state at the start of
+//     the batch: sites i = U[a], j = D[b], their neighbours and the change of
+//     k;
+//   resolve -- while the walker stays in its bin, step m sees that bin's ln g
+//     plus F for every step in between (a rejection and an accepted exchange
+//     with the same k both visit the current bin), so every lane tests its own
+//     step at once (ln g(target) <= ln g(current) + dmax); a ballot finds the
+//     first accepted step, the rejections before it are committed together,
+//     and the lanes are tested again only when an accepted step changes the
+//     bin or the proposals.
+// An accepted exchange of (i_e, j_e) changes a later proposal in two ways.  If
+// the proposal reuses list slot a_e or b_e its sites are no longer U[a], D[b]:
+// the batch ends there.  If one of i_e, j_e neighbours its sites, its change of
+// k is off by 2 for every such neighbour (i_e turned down, j_e up): the later
+// lanes correct it in place and are tested again.  The exchanges accepted in a
+// batch touch distinct slots and distinct sites, so they are applied together
+// after the resolution.  Random numbers are keyed by t, so the committed chain
+// is the sequential chain, bit for bit, for every S.  Batches never cross a
+// flatness check (t multiple of C) or the end of the slice.
 //
-// The current bin's ln g and histogram are kept in registers (plus a pending
-// count); the bins around it live in a shared-memory window that is written
-// back when the walker re-centres it, at every check and at the end.
+// The current bin's ln g and its visits not yet counted live in registers; the
+// bins around it live in a shared-memory window (ln g, and histogram counts
+// added by one lane when the walker leaves a bin), written back when the
+// walker re-centres it, at every check and at the end.
 #pragma once
 
 #include "wl_device.cuh"
@@ -100,16 +103,23 @@ __device__ void group_stage_step(int64_t* lng, hist_t* hist, int nbins, int m, u
 // Window of ln g / histogram bins a walker keeps in shared memory.  Every
 // proposal lies within z bins of the current bin (|dk| <= 2z), so the window
 // [wb, wb + kWin) is re-centred whenever the current bin comes within z bins of
-// an edge that is not the line's own edge.
-
+// an edge that is not the line's own edge.  Histogram words in the window gain
+// counts only; a bin with a count is marked visited when the window is stored.
+// Counts reaching 2^62 (far beyond any run) are reported as an overflow.
 template <int S>
-__device__ __forceinline__ void window_store(int64_t* wl, hist_t* wh, int64_t* lng, hist_t* hist,
+__device__ __forceinline__ bool window_store(int64_t* wl, hist_t* wh, int64_t* lng, hist_t* hist,
                                              int wb, int wn, int m)
 {
+    bool ovf = false;
     for (int x = m; x < wn; x += S) {
+        hist_t h = wh[x];
+        const hist_t cnt = h & ~kVisited;
+        if (cnt) h |= kVisited;
+        ovf |= cnt >= (1ull << 62);
         lng[wb + x] = wl[x];
-        hist[wb + x] = wh[x];
+        hist[wb + x] = h;
     }
+    return ovf;
 }
 
 template <int S>
@@ -129,35 +139,51 @@ __device__ __forceinline__ int window_base(int bc, int nbins)
     return wb < 0 ? 0 : wb;
 }
 
-__device__ __forceinline__ uint4 philox_step(uint64_t t, uint2 key)
+template <bool DET>
+__device__ __forceinline__ Draw draw_step(uint64_t t, uint2 key, uint32_t ell, uint32_t nd,
+                                          const WalkArgs& A)
 {
-    return philox4x32_10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), 0u, 0u), key);
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), 0u, 0u), key);
+    Draw d;
+    d.a = pick(r.x, ell);
+    d.b = pick(r.y, nd);
+    d.dmax = DET ? dmax_det(r.z, A.table, A.q, A.seg_per_log2) : dmax_prod(r.z, A.inv_u);
+    return d;
+}
+
+template <int S>
+__device__ __forceinline__ Draw shfl_draw(unsigned gmask, const Draw& d, int src)
+{
+    Draw o;
+    o.a = __shfl_sync(gmask, d.a, src);
+    o.b = __shfl_sync(gmask, d.b, src);
+    o.dmax = __shfl_sync(gmask, d.dmax, src);
+    return o;
 }
 
 // Walk line `li` for up to A.slice_moves moves (or to its budget, or to
 // convergence).  perm/sp point at the line's list and spins (shared or global
 // memory); win is the group's window (kWin int64 ln g, then kWin u64 hist).
-// All lanes of the group hold identical copies of the scalar state.  The
-// current bin's ln g, histogram word and pending count live in registers and
-// are authoritative; every other bin is up to date in the window (inside it)
-// or in global memory (outside it).
+// All lanes of the group hold identical copies of the scalar state.
 //
-// Random numbers are double-buffered: lane m holds Philox(t + m) in (r0x, r0y,
-// r0z) and Philox(t + S + m) in (r1x, r1y, r1z).  After a batch commits c
-// steps the buffers are shifted by c with two shuffles, and the lanes whose
-// entry falls past the buffered range draw Philox(t + c + S + m) -- a value
-// the next batch does not use, so its latency overlaps the next batch's work.
+// Draws are double-buffered: lane m holds the draw of step t + m in d0 and of
+// t + S + m in d1.  After a batch commits c steps the buffers shift by c (a
+// plain copy when c = S, the usual case), and the lanes whose entry falls past
+// the buffered range take the draw of step t + c + S + m, computed at the
+// start of the next batch so its latency overlaps that batch's work.
 template <int LAT, int S, bool DET, typename IDX>
 __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned gmask,
-                          IDX* perm, uint32_t* sp, const uint32_t* tab, uint8_t* win)
+                          IDX* perm, uint32_t* sp, uint8_t* win)
 {
     constexpr int zb = Coord<LAT>::zbin;  // largest bin step of one move
     constexpr int ks = Coord<LAT>::kshift;
+    constexpr int zc = Coord<LAT>::z;
     const LineDesc D = A.desc[li];
     LineState* P = A.st + li;
-    int64_t k = P->k, t = P->t, F = P->F, stage = P->stage, accepts = P->accepts;
+    int64_t t = P->t, F = P->F, stage = P->stage, accepts = P->accepts;
     int64_t t_stage = P->t_stage, status = P->status, checks = P->checks;
     int64_t batches = P->batches;
+    int k = (int)P->k;
     if (status != 0) return;
     const int ell = D.ell, nbins = D.nbins;
     const uint32_t nd = (uint32_t)(A.g.N - ell);
@@ -169,21 +195,19 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
     int64_t end = t + A.slice_moves;
     if (end > A.budget) end = A.budget;
 
-    int bc = (int)(k >> ks);
+    int bc = k >> ks;
     int wb = window_base(bc, nbins);
     const int wn = nbins < kWin ? nbins : kWin;
     window_load<S>(wl, wh, lng, hist, wb, wn, m);
     __syncwarp(gmask);
-    int64_t cur = wl[bc - wb];
-    hist_t hcur = wh[bc - wb];
-    uint32_t pend = 0;
+    int64_t cur = wl[bc - wb];    // ln g of the current bin, every visit included
+    int pend = 0;                 // visits to the current bin not yet in the window
     int stop = 0;
-    bool by_rounds = false;               // resolution chosen from the acceptance rate
-    int rate_acc = 0, rate_steps = 0;
+    int64_t mF = (int64_t)m * F;
 
-    uint4 r0 = philox_step((uint64_t)(t + m), key);
-    uint4 r1 = make_uint4(0u, 0u, 0u, 0u);
-    uint64_t tf = (uint64_t)(t + S + m);   // pending draw for r1
+    Draw d0 = draw_step<DET>((uint64_t)(t + m), key, (uint32_t)ell, nd, A);
+    Draw d1{};
+    uint64_t tf = (uint64_t)(t + S + m);   // pending draw for d1
     bool needf = true;
 
     while (t < end && !stop) {
@@ -194,195 +218,97 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
         while (left > 0) {
             const int lim = left < S ? left : S;
             // the pending draw (independent of this batch)
-            const uint4 rf = philox_step(tf, key);
-            // -- parallel phase: lane m proposes step t + m against the state at
-            //    the start of the batch (list slots a, b, sites i, j, their
-            //    neighbours and the change of k)
-            const uint32_t a = pick(r0.x, (uint32_t)ell);
-            const uint32_t b = pick(r0.y, nd);
+            const Draw df = draw_step<DET>(tf, key, (uint32_t)ell, nd, A);
+            // -- propose: step t + m against the state at the start of the batch
+            const uint32_t a = d0.a, b = d0.b;
             const uint32_t i = (uint32_t)perm[a];
             const uint32_t j = (uint32_t)perm[ell + b];
-            constexpr int zc = Coord<LAT>::z;
             uint32_t ni[zc], nj[zc];
-            const int dk = delta_k_nb<LAT>(A.g, sp, i, j, ni, nj);
-            if (needf) r1 = rf;
-            // -- resolution: the steps in order with Eq. 3 against the current k
-            //    and ln g (every lane holds the same walker state).  An accepted
-            //    exchange of (i_s, j_s) leaves a later proposal exact unless it
-            //    reuses list slot a_s or b_s or one of i_s, j_s neighbours its
-            //    sites; such proposals are marked, and the batch ends at the
-            //    first marked one.  Two equivalent ways, chosen per walker:
-            unsigned inv = 0u, accm = 0u;
-            int c = lim;
-            if (A.resolve == 2 || (A.resolve == 0 && by_rounds)) {
-                // Rounds.  While the walker keeps its bin, step m sees the state
-                // of step e0 with F added once per step in between (a rejection
-                // or an accepted exchange with dk = 0 both visit the current
-                // bin), so every lane tests its own step at once.  The first lane
-                // that accepts, leaves the window or was marked ends the round,
-                // and the rejections before it are committed together.  Lanes
-                // are tested again only after an accepted step changes the bin.
-                const unsigned live = lim >= 32 ? 0xffffffffu : ((1u << lim) - 1u);
-                unsigned evb = 0u;
-                int pk = 0;                // (dk + 64) << 2 | kind of this lane's step
-                long long lpm = 0;         // ln g of its target bin
-                int e0 = 0;
-                bool eval = true;
-                for (int round = 0; ; ++round) {
-                    if (round > S) {       // cannot happen: e0 grows every round
-                        stop = 4;
-                        c = e0;
-                        break;
-                    }
-                    if (eval) {
-                        // kind: 0 accepted, 1 off the window, 2 outside the line,
-                        // -1 rejected; without branches (a bin outside the window
-                        // reads the current bin's slot, always inside, and is
-                        // not used; dk = 0 is accepted)
-                        const int bp = ((int)k + dk) >> ks;
-                        const int wx = bp - wb;
-                        const bool brk = (unsigned)bp >= (unsigned)nbins;
-                        const bool off = (unsigned)wx >= (unsigned)wn;
-                        lpm = wl[(brk || off) ? bc - wb : wx];
-                        const int64_t d = lpm - (cur + (int64_t)(m - e0) * F);
-                        const bool up = accept_uphill<DET>(d, r0.z, tab, A.q, A.neg_u_log2e);
-                        const int kind = dk == 0 ? 0 : brk ? 2 : off ? 1 : (d <= 0 || up) ? 0 : -1;
-                        pk = ((dk + 64) << 2) | (kind & 3);
-                        evb = group_ballot<S>(gmask, gbase, kind >= 0);
-                        eval = false;
-                    }
-                    const unsigned ev = (evb | inv) & live & ~((1u << e0) - 1u);
-                    if (ev == 0u) {        // the rest of the batch is rejected
-                        cur += (int64_t)(lim - e0) * F;
-                        pend += (uint32_t)(lim - e0);
-                        break;
-                    }
-                    const int e = __ffs(ev) - 1;
-                    cur += (int64_t)(e - e0) * F;      // rejections e0 .. e-1
-                    pend += (uint32_t)(e - e0);
-                    const unsigned bit = 1u << e;
-                    if (inv & bit) {
-                        c = e;
-                        break;
-                    }
-                    const int src = gbase + e;
-                    const int code = __shfl_sync(gmask, pk, src);
-                    const int64_t lpe = __shfl_sync(gmask, lpm, src);
-                    if ((code & 3) == 2) {             // invariant broken
-                        stop = 4;
-                        c = e;
-                        break;
-                    }
-                    if ((code & 3) == 1) {             // walked off the window
-                        c = e;
-                        break;
-                    }
-                    accm |= bit;
-                    const int dke = (code >> 2) - 64;
-                    if (dke != 0) {
-                        // leave the current bin: its ln g and histogram go to the window
-                        const int kp = (int)k + dke;
-                        if ((hcur & ~kVisited) + pend >= kVisited) stop = 2;
-                        if (pend) hcur = (hcur + pend) | kVisited;
-                        wl[bc - wb] = cur;
-                        wh[bc - wb] = hcur;
-                        k = kp;
-                        bc = kp >> ks;
-                        cur = lpe + F;
-                        hcur = wh[bc - wb];
-                        pend = 1u;
+            int dk = delta_k_nb<LAT>(A.g, sp, i, j, ni, nj);
+            if (needf) d1 = df;
+            // accepted iff ln g(target) <= ln g(current before step m) + dmax, and
+            // ln g(current before step m) = u + m F while the walker keeps its bin
+            const int64_t base = mF + d0.dmax;
+            // -- resolve
+            const unsigned live = lim >= 32 ? 0xffffffffu : ((1u << lim) - 1u);
+            int64_t u = cur;      // ln g of the current bin before step 0, shifted as above
+            int ent = -pend;      // batch step at which the walker entered its bin
+            unsigned inv = 0u, accm = 0u, evb = 0u;
+            int e0 = 0, c = lim;
+            bool eval = true;
+            int pk = 0;           // (dk + 64) << 1 | target outside the window
+            int64_t v = 0;        // ln g of the target bin - m F
+            for (;;) {
+                if (eval) {
+                    // a target outside the window reads the current bin's slot
+                    // (always inside) and ends the batch if it is reached
+                    const int bp = (k + dk) >> ks;
+                    const int wx = bp - wb;
+                    const bool off = (unsigned)wx >= (unsigned)wn;
+                    const int64_t ld = wl[off ? bc - wb : wx];
+                    const bool acc = dk == 0 || (!off && ld <= u + base);
+                    pk = ((dk + 64) << 1) | (int)off;
+                    v = ld - mF;
+                    evb = group_ballot<S>(gmask, gbase, acc || off);
+                    eval = false;
+                }
+                const unsigned ev = (evb | inv) & live & ~((1u << e0) - 1u);
+                if (ev == 0u) break;                 // steps e0 .. lim-1 rejected
+                const int e = __ffs(ev) - 1;
+                if ((inv >> e) & 1u) {               // reuses a slot of an accepted exchange
+                    c = e;
+                    break;
+                }
+                const int src = gbase + e;
+                const int pke = __shfl_sync(gmask, pk, src);
+                const int dke = (pke >> 1) - 64;
+                if (pke & 1) {                       // walked off the window
+                    if ((unsigned)((k + dke) >> ks) >= (unsigned)nbins) stop = 4;   // invariant broken
+                    c = e;
+                    break;
+                }
+                const int64_t ve = __shfl_sync(gmask, v, src);
+                const uint32_t ae = __shfl_sync(gmask, a, src), be = __shfl_sync(gmask, b, src);
+                const uint32_t ie = __shfl_sync(gmask, i, src), je = __shfl_sync(gmask, j, src);
+                accm |= 1u << e;
+                if (dke != 0) {
+                    // leave the current bin: steps e0 .. e-1 were rejections in it
+                    wl[bc - wb] = u + (int64_t)e * F;
+                    if (m == 0) atomicAdd(reinterpret_cast<unsigned long long*>(wh + (bc - wb)),
+                                          (unsigned long long)(e - ent));
+                    k += dke;
+                    bc = k >> ks;
+                    u = ve;
+                    ent = e;
+                    eval = true;
+                }
+                if (e + 1 < lim) {
+                    // later proposals: a reused slot ends the batch there, a
+                    // neighbouring exchange shifts their change of k
+                    const bool later = m > e;
+                    const bool slot = (a == ae) | (b == be);
+                    bool nbh = false;
+#pragma unroll
+                    for (int q = 0; q < zc; ++q)
+                        nbh |= (ni[q] == ie) | (ni[q] == je) | (nj[q] == ie) | (nj[q] == je);
+                    inv |= group_ballot<S>(gmask, gbase, later && slot);
+                    if (group_ballot<S>(gmask, gbase, later && nbh)) {
+                        int cor = 0;
+#pragma unroll
+                        for (int q = 0; q < zc; ++q)
+                            cor += (int)(nj[q] == ie) - (int)(ni[q] == ie) + (int)(ni[q] == je) -
+                                   (int)(nj[q] == je);
+                        dk += 2 * cor;
                         eval = true;
-                    } else {
-                        cur += F;
-                        pend += 1u;
-                    }
-                    // later proposals that the accepted exchange of (i_e, j_e) affects
-                    const uint32_t as = __shfl_sync(gmask, a, src), bs = __shfl_sync(gmask, b, src);
-                    const uint32_t is = __shfl_sync(gmask, i, src), js = __shfl_sync(gmask, j, src);
-                    bool conf = (a == as) | (b == bs);
-#pragma unroll
-                    for (int q = 0; q < zc; ++q)
-                        conf |= (ni[q] == is) | (ni[q] == js) | (nj[q] == is) | (nj[q] == js);
-                    inv |= group_ballot<S>(gmask, gbase, conf && m > e);
-                    e0 = e + 1;
-                    if (stop) {
-                        c = e0;
-                        break;
-                    }
-                    if (e0 >= lim) break;
-                }
-            } else {
-                // Steps one at a time; step s's change of k and random word are
-                // shuffled one step ahead.
-                int dkn = __shfl_sync(gmask, dk, gbase);
-                uint32_t rzn = __shfl_sync(gmask, r0.z, gbase);
-                for (int s = 0; s < lim; ++s) {
-                    const int src = gbase + s;
-                    const int dks = dkn;
-                    const uint32_t rzs = rzn;
-                    const int nxt = gbase + (s + 1 < S ? s + 1 : s);
-                    dkn = __shfl_sync(gmask, dk, nxt);
-                    rzn = __shfl_sync(gmask, r0.z, nxt);
-                    if ((inv >> s) & 1u) {
-                        c = s;
-                        break;
-                    }
-                    const int kp = (int)k + dks;
-                    bool acc = true;
-                    int64_t lp = 0;
-                    if (dks != 0) {
-                        const int bp = kp >> ks;
-                        const int wx = bp - wb;
-                        if ((unsigned)bp >= (unsigned)nbins) {      // invariant broken
-                            stop = 4;
-                            c = s;
-                            break;
-                        }
-                        if ((unsigned)wx >= (unsigned)wn) {        // walked off the window
-                            c = s;
-                            break;
-                        }
-                        lp = wl[wx];
-                        const int64_t d = lp - cur;
-                        acc = d <= 0 || accept_uphill<DET>(d, rzs, tab, A.q, A.neg_u_log2e);
-                    }
-                    if (!acc) {
-                        cur += F;
-                        pend += 1u;
-                        continue;
-                    }
-                    accm |= 1u << s;
-                    if (dks != 0) {
-                        // leave the current bin: its ln g and histogram go to the window
-                        if ((hcur & ~kVisited) + pend >= kVisited) stop = 2;
-                        if (pend) hcur = (hcur + pend) | kVisited;
-                        wl[bc - wb] = cur;
-                        wh[bc - wb] = hcur;
-                        k = kp;
-                        bc = kp >> ks;
-                        cur = lp + F;
-                        hcur = wh[bc - wb];
-                        pend = 1u;
-                    } else {
-                        cur += F;
-                        pend += 1u;
-                    }
-                    // later proposals that the accepted exchange of (i_s, j_s) affects
-                    const uint32_t as = __shfl_sync(gmask, a, src), bs = __shfl_sync(gmask, b, src);
-                    const uint32_t is = __shfl_sync(gmask, i, src), js = __shfl_sync(gmask, j, src);
-                    bool conf = (a == as) | (b == bs);
-#pragma unroll
-                    for (int q = 0; q < zc; ++q)
-                        conf |= (ni[q] == is) | (ni[q] == js) | (nj[q] == is) | (nj[q] == js);
-                    inv |= group_ballot<S>(gmask, gbase, conf && m > s);
-                    if (stop) {
-                        c = s + 1;
-                        break;
                     }
                 }
+                e0 = e + 1;
+                if (e0 >= lim) break;
             }
-            if (c == 0) stop = 4;                  // lane 0 is always evaluable
-            // apply the accepted exchanges (mutually independent) to lists and spins
+            cur = u + (int64_t)c * F;
+            pend = c - ent;
+            if (c == 0) stop = 4;                  // step t always fits the window
+            // apply the accepted exchanges (distinct slots, distinct sites)
             if ((accm >> m) & 1u) {
                 perm[a] = (IDX)j;
                 perm[ell + b] = (IDX)i;
@@ -390,37 +316,30 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
                 atomicOr(&sp[j >> 5], 1u << (j & 31u));
             }
             accepts += __popc(accm);
-            // rounds pay per accepted step, single steps per step: pick rounds
-            // while fewer than half of the recent steps were accepted
-            rate_acc += __popc(accm);
-            rate_steps += c;
-            if (rate_steps >= 512) {
-                by_rounds = 2 * rate_acc < rate_steps;
-                rate_acc = rate_steps = 0;
-            }
             __syncwarp(gmask);
             if ((bc - zb < wb && wb > 0) || (bc + zb >= wb + kWin && wb + kWin < nbins)) {
                 // re-centre the window (the current bin stays in registers)
-                window_store<S>(wl, wh, lng, hist, wb, wn, m);
+                if (group_ballot<S>(gmask, gbase, window_store<S>(wl, wh, lng, hist, wb, wn, m))) stop = 2;
                 __syncwarp(gmask);
                 wb = window_base(bc, nbins);
                 window_load<S>(wl, wh, lng, hist, wb, wn, m);
                 __syncwarp(gmask);
             }
-            // shift the random-number buffers by c: lane m now needs steps
-            // t + c + m (r0) and t + c + S + m (r1)
-            {
+            // shift the draw buffers by c: lane m now needs steps t + c + m (d0)
+            // and t + c + S + m (d1)
+            if (c == S) {
+                d0 = d1;
+                needf = true;
+            } else {
                 const int srcm = m + c;                       // < 2S
                 const int sl = gbase + (srcm & (S - 1));
-                const uint32_t ax = __shfl_sync(gmask, r0.x, sl), ay = __shfl_sync(gmask, r0.y, sl),
-                               az = __shfl_sync(gmask, r0.z, sl);
-                const uint32_t bx = __shfl_sync(gmask, r1.x, sl), by = __shfl_sync(gmask, r1.y, sl),
-                               bz = __shfl_sync(gmask, r1.z, sl);
+                const Draw x0 = shfl_draw<S>(gmask, d0, sl);
+                const Draw x1 = shfl_draw<S>(gmask, d1, sl);
                 needf = srcm >= S;
-                r0 = needf ? make_uint4(bx, by, bz, 0u) : make_uint4(ax, ay, az, 0u);
-                r1 = make_uint4(bx, by, bz, 0u);
-                tf = (uint64_t)(t + c + S + m);
+                d0 = needf ? x1 : x0;
+                d1 = x1;
             }
+            tf = (uint64_t)(t + c + S + m);
             t += c;
             left -= c;
             batches += 1;
@@ -430,18 +349,17 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
 
         if (t == next_check) {
             // current bin -> window -> global, then test flatness over the line
-            if ((hcur & ~kVisited) + pend >= kVisited) {
+            __syncwarp(gmask);
+            if (m == 0) {
+                wl[bc - wb] = cur;
+                wh[bc - wb] += (hist_t)pend;
+            }
+            pend = 0;
+            __syncwarp(gmask);
+            if (group_ballot<S>(gmask, gbase, window_store<S>(wl, wh, lng, hist, wb, wn, m))) {
                 stop = 2;
                 break;
             }
-            if (pend) hcur = (hcur + pend) | kVisited;
-            pend = 0;
-            if (m == 0) {
-                wl[bc - wb] = cur;
-                wh[bc - wb] = hcur;
-            }
-            __syncwarp(gmask);
-            window_store<S>(wl, wh, lng, hist, wb, wn, m);
             __syncwarp(gmask);
             checks += 1;
             const bool flat = group_flat<S>(hist, nbins, m, gmask, A.flat_pm);
@@ -452,17 +370,16 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
                 window_load<S>(wl, wh, lng, hist, wb, wn, m);
                 __syncwarp(gmask);
                 cur = wl[bc - wb];
-                hcur = wh[bc - wb];
             }
             if (flat) {
                 group_stage_step<S>(lng, hist, nbins, m, gmask);
                 F >>= 2;                     // ln f -> ln f / 4
+                mF = (int64_t)m * F;
                 stage += 1;
                 t_stage = t;
                 window_load<S>(wl, wh, lng, hist, wb, wn, m);
                 __syncwarp(gmask);
                 cur = wl[bc - wb];
-                hcur = wh[bc - wb];
                 if (F == 0) {                // ln f < ln f_min
                     status = 1;
                     break;
@@ -481,13 +398,14 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
     }
     // current bin -> window -> global
     if (stop != 4) {
-        if (pend) hcur = (hcur + pend) | kVisited;
+        __syncwarp(gmask);
         if (m == 0) {
             wl[bc - wb] = cur;
-            wh[bc - wb] = hcur;
+            wh[bc - wb] += (hist_t)pend;
         }
         __syncwarp(gmask);
-        window_store<S>(wl, wh, lng, hist, wb, wn, m);
+        if (group_ballot<S>(gmask, gbase, window_store<S>(wl, wh, lng, hist, wb, wn, m)) && stop == 0)
+            stop = 2;
     }
     if (stop == 2) status = 2;
     if (stop == 4) status = 3;
@@ -531,17 +449,13 @@ template <int LAT, int S, bool DET, typename IDX>
 __global__ void walk_kernel(const WalkArgs A)
 {
     extern __shared__ __align__(16) uint8_t smem[];
-    uint32_t* tab = reinterpret_cast<uint32_t*>(smem);
-    for (int x = threadIdx.x; x < kTableN; x += blockDim.x) tab[x] = A.table[x];
-    __syncthreads();
-
     const int lane = threadIdx.x & 31;
     const int m = lane % S;
     const int gbase = lane - m;
     const unsigned gmask = group_mask<S>(gbase);
     const int gid = threadIdx.x / S;
     // per-group slot: window, then (when staged) the list and the spins
-    uint8_t* slot = smem + kTableBytes + (size_t)gid * (size_t)A.slot_bytes;
+    uint8_t* slot = smem + (size_t)gid * (size_t)A.slot_bytes;
     uint8_t* win = slot;
     slot += kWinBytes;
     // per-line strides are padded to 16 bytes: pstride list entries, W spin words
@@ -564,13 +478,13 @@ __global__ void walk_kernel(const WalkArgs A)
                           perm_words, m);
             group_copy<S>(ssp, gsp, W, m);
             __syncwarp(gmask);
-            walk_line<LAT, S, DET, IDX>(A, li, m, gbase, gmask, sperm, ssp, tab, win);
+            walk_line<LAT, S, DET, IDX>(A, li, m, gbase, gmask, sperm, ssp, win);
             group_copy<S>(reinterpret_cast<uint32_t*>(gperm), reinterpret_cast<const uint32_t*>(sperm),
                           perm_words, m);
             group_copy<S>(gsp, ssp, W, m);
             __syncwarp(gmask);
         } else {
-            walk_line<LAT, S, DET, IDX>(A, li, m, gbase, gmask, gperm, gsp, tab, win);
+            walk_line<LAT, S, DET, IDX>(A, li, m, gbase, gmask, gperm, gsp, win);
         }
     }
 }

@@ -143,27 +143,63 @@ def test_other_lattices_bit_exact(lattice, L, budget):
         assert_line_equal(h, ell, ref[ell], lattice)
 
 
-@pytest.mark.parametrize("resolve", [1, 2])
-@pytest.mark.parametrize("mapping", [1, 8, 32])
-def test_square_L12_bit_exact_each_resolution(l12_ref, resolve, mapping):
-    """Both ways of resolving a batch (one step at a time; rounds that commit
-    the rejections up to the next accepted step at once), forced for the whole
-    walk, give the oracle's chain."""
-    h = run_gpu("square", 12, 1, 1e-8, 1000, 10**7, mapping=mapping, resolve=resolve)
-    for ell in range(73):
-        assert_line_equal(h, ell, l12_ref[ell], f"S={mapping} resolve={resolve}")
-
-
-@pytest.mark.parametrize("resolve", [1, 2])
-@pytest.mark.parametrize("lattice,L,mapping", [("triangular", 6, 32), ("cubic", 4, 8),
-                                               ("square_open", 7, 32), ("square_open", 16, 4)])
-def test_other_lattices_each_resolution(lattice, L, mapping, resolve):
-    budget = 300_000
-    h = run_gpu(lattice, L, 9, 1e-6, 777, budget, mapping=mapping, resolve=resolve)
+@pytest.mark.parametrize("lattice,L,mapping", [("square", 3, 32), ("square", 4, 32), ("square", 5, 16),
+                                               ("triangular", 3, 32), ("triangular", 4, 8),
+                                               ("cubic", 3, 32), ("square_open", 3, 32),
+                                               ("square_open", 4, 16)])
+def test_dense_conflicts_bit_exact(lattice, L, mapping):
+    """Tiny lattices, where an accepted exchange often neighbours the later
+    proposals of its batch (their change of k is corrected in place) or reuses
+    their list slot (the batch ends there), and every line from l = 1 up: the
+    oracle's chain bit for bit, in both acceptance modes' deterministic form."""
+    budget = 200_000
+    h = run_gpu(lattice, L, 13, 1e-6, 1000, budget, mapping=mapping)
     N = h.N
-    ref = oracle_lines(LAT[lattice], L, range(N // 2 + 1), 9, 1e-6, 777, budget)
+    ref = oracle_lines(LAT[lattice], L, range(N // 2 + 1), 13, 1e-6, 1000, budget)
     for ell in range(N // 2 + 1):
-        assert_line_equal(h, ell, ref[ell], f"{lattice} resolve={resolve}")
+        assert_line_equal(h, ell, ref[ell], f"{lattice} L={L} S={mapping}")
+    st = h.stats()
+    assert st["accepts"] > 0
+
+
+@pytest.mark.parametrize("u", [0.5, 1e-3, 1e-6, 1e-7, 1e-8, 1e-10])
+def test_accept_threshold_inverts_the_table(u):
+    """Eq. 3 as the walker evaluates it: dmax(r) is the largest ln g increase
+    the random word r accepts.  Against the oracle's T(d): r < T(dmax) (or
+    dmax = 0) and r >= T(dmax + 1), for random words and the hard ones (0, 1,
+    small words near the table's tail, words equal to and next to entries)."""
+    table, q = oracle.exp_table(u)
+    rng = np.random.default_rng(7)
+    words = [0, 1, 2, 3, 255, 65535, 65536, 2**31, 2**32 - 1, 2**32 - 2]
+    words += [int(x) for x in rng.integers(0, 2**32, 300)]
+    words += [int(x) for x in rng.integers(0, 2**16, 60)]
+    for i in list(range(1, 40)) + list(range(4000, 4096)) + [int(x) for x in rng.integers(1, 4096, 40)]:
+        for dv in (-1, 0, 1):
+            w = int(table[i]) + dv
+            if 0 <= w < 2**32:
+                words.append(w)
+    r = np.array(words, dtype=np.uint32)
+    dm = wl.wl_accept_threshold(u, 1, r)
+    for w, d in zip(words, dm):
+        d = int(d)
+        assert 0 <= d < (4095 << q)
+        assert d == 0 or w < oracle.threshold(u, d), (u, w, d)
+        assert w >= oracle.threshold(u, d + 1), (u, w, d)
+
+
+def test_accept_threshold_production():
+    """Production form: dmax = floor(-ln U / u), U = (r/2^8 + 1/2) 2^-24, to FP32
+    precision (relative 1e-6), also for U next to 1 where 1 - U is tiny; every
+    word accepts d <= 0."""
+    rng = np.random.default_rng(3)
+    r = np.concatenate([np.array([0, 255, 256, 2**31, 2**32 - 1, 2**32 - 256, 2**32 - 4096, 2**31 + 2**30], dtype=np.uint32),
+                        rng.integers(0, 2**32, 2000, dtype=np.uint64).astype(np.uint32)])
+    for u in (1e-6, 1e-8):
+        dm = wl.wl_accept_threshold(u, 0, r).astype(np.float64)
+        U = ((r >> 8).astype(np.float64) + 0.5) * 2.0**-24
+        exact = -np.log(U) / u
+        assert np.all(dm >= 0)
+        assert np.all(np.abs(dm - exact) <= 1e-6 * exact + 1.5)
 
 
 def test_square_L64_sampled_lines_bench_launch():

@@ -49,11 +49,6 @@ def test_host_side_validation_without_gpu(lib):
         h.set_option("mapping", 3)
     with pytest.raises(wl.WLError):
         h.set_option("no_such_option", 1)
-    for v in (0, 1, 2):
-        h.set_option("resolve", v)
-        assert h.get_option("resolve") == v
-    with pytest.raises(wl.WLError):
-        h.set_option("resolve", 3)
     with pytest.raises(wl.WLError):
         wl.Handle("square", 2)                         # L < 3 has double bonds
     h.close()

@@ -450,3 +450,125 @@ def test_same_f_resets_keeps_the_walk_exact_and_accurate():
             errs.append(np.abs(lg[ks // 2] - np.log(g[ks, ell])))
     errs = np.concatenate(errs)
     assert errs.mean() <= 0.05
+
+
+# --------------------------------------------------------------------------
+# Flatness (the 80%/80% convention of the WL recap): hand-built histograms at
+# the boundary of the rule, so that a misreading of it fails here
+# --------------------------------------------------------------------------
+
+def _flat(counts, visited=None, flat_pm=800):
+    counts = np.asarray(counts, dtype=np.int64)
+    vis = np.ones(counts.size, np.uint8) if visited is None else np.asarray(visited, np.uint8)
+    return oracle.is_flat(counts, vis, flat_pm)
+
+
+def test_flatness_fraction_of_bins_boundary():
+    """Flat iff at least 80% of the visited bins reach 80% of the mean: with
+    10 visited bins, 8 high ones is flat (at least, not more than), 7 is not."""
+    assert _flat([100] * 8 + [0] * 2)          # mean 80, 8 of 10 bins >= 64
+    assert not _flat([100] * 7 + [0] * 3)      # mean 70, 7 of 10 bins >= 56
+    assert _flat([100] * 10)
+    assert not _flat([1] + [0] * 9)
+
+
+def test_flatness_bin_exactly_at_the_threshold_counts():
+    """A bin holding exactly 80% of the mean passes (>=, not >): 7 bins of 23,
+    one of 14 and two empty give mean 17.5 and threshold 14, so 8 of 10 pass."""
+    assert _flat([23] * 7 + [14] + [0] * 2)
+    assert not _flat([23] * 7 + [13] + [0] * 2)
+
+
+def test_flatness_counts_visited_bins_only():
+    """Never-visited bins (reachable-set gaps, or bins not yet found) are left
+    out of n and of the mean: the 4x4 line l = 8 has no k = 10, 28, 30, and
+    here its walker has not found k = 32 yet."""
+    ks = np.arange(0, 33, 2)
+    vis = np.array([k not in (10, 28, 30, 32) for k in ks], np.uint8)
+    counts = np.where(vis == 1, 50, 0)
+    assert _flat(counts, vis)
+    # the same counts judged over all 17 bins would not be flat (13 of 17 < 80%)
+    assert not _flat(counts, np.ones(ks.size, np.uint8))
+    # a visited bin with an empty histogram in this stage does take part
+    assert not _flat([9] * 7 + [0] * 3, np.ones(10, np.uint8))
+    assert _flat([9] * 7 + [0] * 3, np.array([1] * 7 + [0] * 3, np.uint8))
+
+
+def test_flatness_fraction_applies_to_both_counts():
+    """x = 0.5: at least half of the bins at 0.5 x mean.  Counts 4 x 10, 2 x 3,
+    4 x 0: mean 4.6; 6 bins >= 2.3 -> flat; with 0.8 x mean for the bin test
+    (3.68) only 4 pass, and with an 80% bin fraction 6 of 10 would not do."""
+    c = [10] * 4 + [3] * 2 + [0] * 4
+    assert _flat(c, flat_pm=500)
+    assert not _flat(c, flat_pm=800)
+    assert _flat([10] * 5 + [0] * 5, flat_pm=500)
+    assert not _flat([10] * 4 + [0] * 6, flat_pm=500)
+
+
+def test_flatness_exact_for_huge_counts():
+    """Counts near 2^60, where 1000 n h passes 2^64: the boundary case above
+    scaled by 2^55 (7 bins of 23 2^55, one at exactly 80% of the mean, 14 2^55,
+    two empty) is still decided exactly, one count below it is not flat."""
+    big = 2**55
+    assert _flat([23 * big] * 7 + [14 * big] + [0] * 2)
+    assert not _flat([23 * big] * 7 + [14 * big - 1] + [0] * 2)
+    assert not _flat([0, 0, 0], np.zeros(3, np.uint8))   # nothing visited: never flat
+
+
+# --------------------------------------------------------------------------
+# The 3x3x3 simple cubic lattice (tests/golden/cubic_L3_exact.txt, full
+# enumeration of its 2^27 configurations by the oracle's brute force)
+# --------------------------------------------------------------------------
+
+def _cubic_l3_exact():
+    g = np.zeros((82, 28))
+    with open(os.path.join(HERE, "golden", "cubic_L3_exact.txt")) as f:
+        for line in f:
+            if not line.startswith("#"):
+                ell, k, v = line.split()
+                g[int(k), int(ell)] = float(v)
+    return g
+
+
+def test_golden_cubic_l3_closed_forms():
+    """The stored cubic surface against what holds on any lattice without
+    double bonds (z = 6, N = 27, N_B = 81): row sums C(N, l), l <-> N - l
+    symmetry, g(0|0) = 1, g(z|1) = N, g(2z-2|2) = N_B, g(2z|2) = C(N,2) - N_B,
+    k_max(l) <= z min(l, N - l), and only even k (k = zl - 2 e(up set))."""
+    g = _cubic_l3_exact()
+    for ell in range(28):
+        assert g[:, ell].sum() == math.comb(27, ell)
+        assert np.array_equal(g[:, ell], g[:, 27 - ell])
+        ks = np.nonzero(g[:, ell])[0]
+        assert np.all(ks % 2 == 0)
+        assert ks.max() <= 6 * min(ell, 27 - ell)
+    assert g[0, 0] == 1 and g[6, 1] == 27
+    assert g[10, 2] == 81 and g[12, 2] == math.comb(27, 2) - 81
+
+
+def test_wl_accuracy_cubic_l3_against_enumeration():
+    """The oracle's walk (production mode, ln f_min = 1e-8, checks every 10^6
+    moves) on all 14 lines of the 3^3 torus, 4 seeds: away from each line's
+    two lowest and two highest k within mean 0.02 / max 0.1 of the exact
+    ln g_kl; the ends, where the walker spends least time (the remark after
+    Eq. 4), reported separately within mean 0.05 / max 0.3."""
+    from concurrent.futures import ThreadPoolExecutor
+    g = _cubic_l3_exact()
+
+    def one(args):
+        seed, ell = args
+        st = oracle.run_line(oracle.CUBIC, 3, ell, seed, 1e-8, 10**6, mode=1)
+        assert st.converged
+        lg = oracle.assemble(27, ell, st.lng, st.visited, 1e-8)
+        ks = np.nonzero(g[:, ell])[0]
+        d = np.abs(lg[ks // 2] - np.log(g[ks, ell]))
+        inner = np.zeros(d.size, bool)
+        inner[2:-2] = True
+        return d[inner], d[~inner]
+
+    with ThreadPoolExecutor(max(1, os.cpu_count() or 1)) as ex:
+        res = list(ex.map(one, [(s, l) for s in range(1, 5) for l in range(14)]))
+    inner = np.concatenate([r[0] for r in res])
+    ends = np.concatenate([r[1] for r in res])
+    assert inner.mean() <= 0.02 and inner.max() <= 0.1
+    assert ends.mean() <= 0.05 and ends.max() <= 0.3

@@ -9,8 +9,9 @@ library.  Here the test plays that caller: it allocates the buffers itself
 (with torch), calls the entry point twice in a row (initialise and walk, then
 continue the same walk) and checks that the walker state after each call is
 identical to what the handle API (wl_create / wl_run) produces on the same
-inputs.  Deterministic mode, so identical means bit for bit, the tolerance of
-the other parity tests.
+inputs; it also walks a lattice to convergence over several of the entry
+point's slices and fills the buffers of a full 64x64 surface.  Deterministic
+mode, so identical means bit for bit, the tolerance of the other parity tests.
 """
 import ctypes
 
@@ -94,6 +95,53 @@ def test_noalloc_two_calls_match_handle_api(lattice, L, ell_first, nlines):
             got, ref = buf.line(i), h.line_state(ell_first + i)
             for key in ref:
                 assert np.array_equal(got[key], ref[key]), (call, ell_first + i, key)
+    h.close()
+
+
+def test_noalloc_walks_several_slices_to_convergence():
+    """Checks every 2^18 moves: every 4x4 line needs 14 stages (ln f_min =
+    1e-8), more than three of the entry point's 2^20-move slices, so its slice
+    loop restarts the queue and re-reads the summary several times; the call
+    returns WL_OK with the handle API's converged state, bit for bit."""
+    import torch
+    f = _fn()
+    seed, u, C = 5, 1e-8, 1 << 18
+    buf = Buffers("square", 4, 0, 9)
+    rc = f(wl.WL_SQUARE, 4, 0, 9, seed, 1, u, 0.8, C, 2**62, 8, 1, *buf.ptrs(), buf.stream)
+    assert rc == wl.WL_OK, wl.wl_last_error()
+    torch.cuda.synchronize()
+    h = wl.Handle("square", 4, seed=seed, check_interval=C, mapping=8)
+    assert h.run(u, 0.8) == wl.WL_OK
+    for i in range(9):
+        got, ref = buf.line(i), h.line_state(i)
+        assert i == 0 or got["sc"][1] > 3 << 20          # l = 0 has no move
+        for key in ref:
+            assert np.array_equal(got[key], ref[key]), (i, key)
+    h.close()
+
+
+def test_noalloc_full_64x64_surface_layout():
+    """All 2049 lines of the 64x64 lattice in one call (near the 4096-line
+    limit of the scratch), a short budget, then a continuation: sampled lines
+    equal the handle API's, and a continuation with another ln_f_min is refused."""
+    import torch
+    f = _fn()
+    seed, u, C = 2, 1e-6, 1024
+    buf = Buffers("square", 64, 0, 2049)
+    h = wl.Handle("square", 64, seed=seed, check_interval=C, mapping=8)
+    for call, budget in enumerate((3000, 8192)):
+        rc = f(wl.WL_SQUARE, 64, 0, 2049, seed, 1, u, 0.8, C, budget, 8, 1 if call == 0 else 0,
+               *buf.ptrs(), buf.stream)
+        assert rc == wl.WL_ENOTCONVERGED, wl.wl_last_error()
+        torch.cuda.synchronize()
+        h.set_option("move_budget", budget)
+        h.run(u, 0.8)
+        for i in (1, 2, 3, 100, 511, 1024, 1500, 2047, 2048):
+            got, ref = buf.line(i), h.line_state(i)
+            for key in ref:
+                assert np.array_equal(got[key], ref[key]), (call, i, key)
+    rc = f(wl.WL_SQUARE, 64, 0, 2049, seed, 1, 1e-7, 0.8, C, 9000, 8, 0, *buf.ptrs(), buf.stream)
+    assert rc == wl.WL_EINVAL and "ln_f_min" in wl.wl_last_error()
     h.close()
 
 
