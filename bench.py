@@ -234,8 +234,19 @@ def converge_on_cpu(lat, Lc, lo, hi, args, gpu_moves):
 
 def run_converge(args):
     """Time to ln f_min: one whole surface walked until every line converged
-    (or the time limit), reported as its own JSON line."""
+    (or the time limit), reported as its own JSON line.  Under torchrun the
+    surface is split by lines (LPT on bins^2, paper_1302_2320_gb300.shard):
+    each rank walks its share on its GPU, the assembled lines are gathered on
+    rank 0, and the time is the maximum over ranks."""
     import paper_1302_2320_gb300 as wl
+    from paper_1302_2320_gb300 import shard
+    world, rank, local = _dist()
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+        torch.cuda.set_device(local)
     wl.build()
     lat, Lc = args.lattice, args.converge
     h = wl.Handle(lat, Lc, deterministic=1, check_interval=args.check_interval, seed=1,
@@ -244,36 +255,69 @@ def run_converge(args):
     lo, hi = 0, h.N // 2
     if args.lines:
         lo, hi = (int(x) for x in args.lines.split(":"))
-        h.set_option("ell_min", lo)
-        h.set_option("ell_max", hi)
+    ells = list(range(lo, hi + 1))
+    if world > 1:
+        costs = {l: c for l, c in shard.handle_costs(h).items() if lo <= l <= hi}
+        ells = shard.lpt_partition(costs, world)[rank]
+    h.select_lines(ells)
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     rc = h.run(args.ln_f_min, FLATNESS, allow=(wl.WL_OK, wl.WL_ETIMEOUT))
     sec = time.perf_counter() - t0
     st = h.stats()
+    moves = [0] * (h.N // 2 + 1)
+    for ell in ells:
+        moves[ell] = int(h.line_state(ell)["sc"][1])
+    lines = None
+    if rc == wl.WL_OK or world == 1:
+        h.assemble()
+        lines = {ell: h.get_lng(ell) for ell in ells}
+    if dist:
+        import torch
+        agg = torch.tensor([sec, st["moves"], st["lines_converged"], st["lines"], st["accepts"],
+                            int(rc != wl.WL_OK)], dtype=torch.float64)
+        mx = agg.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(agg, op=dist.ReduceOp.SUM)
+        mv = torch.tensor(moves, dtype=torch.int64)
+        dist.all_reduce(mv, op=dist.ReduceOp.SUM)
+        moves = mv.tolist()
+        sec = float(mx[0])
+        st = dict(st, moves=int(agg[1]), lines_converged=int(agg[2]), lines=int(agg[3]),
+                  accepts=int(agg[4]))
+        failed = int(mx[5])
+        rc = wl.WL_OK if not failed else wl.WL_ETIMEOUT
+        lines = shard.gather_lines(dist, lines or {}) if not failed else None
+        if rank != 0:
+            h.close()
+            dist.destroy_process_group()
+            return 0
     line = {"mode": "time_to_ln_f_min", "lattice": lat, "L": Lc, "N": h.N, "lines": st["lines"],
             "ln_f_min": args.ln_f_min, "check_interval": args.check_interval,
-            "same_f_resets": args.same_f_resets,
+            "same_f_resets": args.same_f_resets, "n_gpus": world,
             "status": "converged" if rc == wl.WL_OK else "time limit",
             "seconds": sec, "lines_converged": st["lines_converged"],
             "min_stage": st["min_stage"], "max_stage": st["max_stage"], "moves": st["moves"],
             "moves_per_s": st["moves"] / sec, "mapping": st["mapping"],
             "accept_rate": st["accepts"] / max(st["moves"], 1)}
-    moves = [0] * (h.N // 2 + 1)
-    for ell in range(lo, hi + 1):
-        moves[ell] = int(h.line_state(ell)["sc"][1])
+    if world > 1:
+        line["parallelism"] = f"lines sharded over {world} ranks (LPT on bins^2), gathered on rank 0"
     line["lines_walked"] = [lo, hi]
     line["moves_to_converge"] = line_moves_summary(moves, h.N)
     if args.cpu_converge and rc == wl.WL_OK:
         line["cpu_oracle"] = converge_on_cpu(lat, Lc, lo, hi, args, moves)
         line["gpu_speedup_over_cpu"] = line["cpu_oracle"]["seconds"] / sec
     exact = os.path.join(ROOT, "tests", "golden", f"square_L{Lc}_gk_exact.txt")
-    if lat == "square" and os.path.exists(exact) and (lo, hi) == (0, h.N // 2):
-        h.assemble()
-        lines = [h.get_lng(ell) for ell in range(h.N // 2 + 1)]
+    if (lat == "square" and os.path.exists(exact) and (lo, hi) == (0, h.N // 2)
+            and rc == wl.WL_OK and lines is not None):
+        surface = [lines[ell] for ell in range(h.N // 2 + 1)]
         line["sum_over_lines_vs_exact_gk"] = exact_gk_comparison(
-            sum_over_lines(lines, h.N), exact, 2 * h.N)
+            sum_over_lines(surface, h.N), exact, 2 * h.N)
     print(json.dumps(line), flush=True)
     h.close()
+    if dist:
+        dist.destroy_process_group()
     return 0
 
 

@@ -84,10 +84,15 @@ typedef struct {
 wl_status wl_create(wl_lattice lattice, int L, wl_handle* out);
 
 /* Device bytes a handle for (lattice, L) will hold once run, or 0 on bad
- * arguments.  Used to admit jobs against a memory budget. */
+ * arguments: the ragged ln g / histogram arrays over each line's bins (Eq. 2's
+ * k range per l) plus walker state.  Used to admit jobs against a memory
+ * budget; the paper has no counterpart. */
 size_t wl_required_bytes(wl_lattice lattice, int L);
 
-/* Set an integer option before (or between) runs.  Keys:
+/* Set an integer option before (or between) runs.  The options are the free
+ * parameters of the walk of the method section (around Eq. 3 and Eq. 4, and
+ * the Wang-Landau recap it builds on: how often flatness is checked, the random
+ * stream, the move cap) and of how the library maps it onto the GPU.  Keys:
  *   "seed"           Philox key word 1 of every walker (default 1)
  *   "deterministic"  1: integer acceptance against the exp threshold table, the
  *                    chain bit-identical to the same walk taken one move at a
@@ -112,7 +117,12 @@ size_t wl_required_bytes(wl_lattice lattice, int L);
 wl_status wl_set_option(wl_handle h, const char* key, int64_t value);
 wl_status wl_get_option(wl_handle h, const char* key, int64_t* value);
 
-/* Run the walks until every selected line has ln f < ln_f_min (returns WL_OK),
+/* The walk of the method section, on every selected line: spin-exchange
+ * proposals that keep l fixed, acceptance min(1, g(k)/g(k')) (Eq. 3),
+ * ln g(k) += ln f and h(k) += 1 at the current k, the flatness test of the
+ * Wang-Landau recap every check_interval moves, and on a flat histogram the
+ * stage step of Eq. 4 (h reset, ln g normalised, ln f -> ln f / 4).
+ * Run the walks until every selected line has ln f < ln_f_min (returns WL_OK),
  * the move budget is reached (WL_ENOTCONVERGED), the timeout elapses
  * (WL_ETIMEOUT) or wl_abort() is called (WL_EABORTED).  ln_f_min in
  * [1e-10, 0.5]; flatness in (0, 1] is the fraction x of the x/x flatness test
@@ -123,31 +133,49 @@ wl_status wl_get_option(wl_handle h, const char* key, int64_t* value);
  * Blocks the calling thread until the run stops. */
 wl_status wl_run(wl_handle h, double ln_f_min, double flatness);
 
+/* Walk only the lines ells[0..n) (each in [0, N/2], in any order; n = 0
+ * restores every line).  Lines are independent walks (the paper's central
+ * point: each micromagnetic line is its own one-dimensional Wang-Landau walk),
+ * so a surface can be split across devices or hosts by lines and gathered
+ * afterwards; a line walked here is bit-identical to the same line walked
+ * with every other line.  Sets ell_min/ell_max to the set's extremes (setting
+ * either option afterwards drops the set).  Before the first run or after
+ * wl_reset (else WL_ESTATE).  wl_get_lng answers for walked lines only;
+ * wl_get_surface covers [ell_min, ell_max], where lines outside the set hold
+ * -inf (no bin visited).  Errors: WL_EINVAL, WL_ESTATE. */
+wl_status wl_select_lines(wl_handle h, const int32_t* ells, int n);
+
 /* Request that a wl_run in progress on another thread stop at its next
- * flatness check.  Safe to call from any thread. */
+ * flatness check.  Safe to call from any thread.  No paper counterpart. */
 wl_status wl_abort(wl_handle h);
 
-/* Discard walker state (keeps allocations); the next wl_run re-initialises. */
+/* Discard walker state (keeps allocations); the next wl_run re-initialises
+ * (the initial state of the method section).  Errors: WL_EINVAL. */
 wl_status wl_reset(wl_handle h);
 
 /* Assemble ln g_kl = ln C(N,l) + ln g(k|l) - ln sum_k' g(k'|l) (Eq. 4 applied
  * once, FP64) for every walked line on the device.  Unvisited k get -inf. */
 wl_status wl_assemble(wl_handle h);
 
-/* Copy line ell (0..N; ell > N/2 is served by its mirror N-ell) of the last
+/* The result of Eq. 4 for one line: ln g_kl, the line's density of states
+ * normalised to C(N, l) (Eq. 2's g_kl; lines l and N-l equal by up-down
+ * symmetry).  Copy line ell (0..N; ell > N/2 is served by its mirror N-ell) of the last
  * wl_assemble into out[0..n), n = number of bins, bin b holding k = k_lo +
  * b*k_step (k_lo = 0; k_step = 2 periodic, 1 open boundaries).  If cap < n nothing is copied, *n_out is
  * set and WL_EINVAL is returned.  Errors: WL_ESTATE before wl_assemble. */
 wl_status wl_get_lng(wl_handle h, int ell, double* out, size_t cap,
                      int* k_lo, int* k_step, size_t* n_out);
 
-/* Copy every walked line's assembled ln g (l = ell_min..ell_max, ragged, in
+/* The whole assembled surface ln g_kl of Eq. 2 / Eq. 4.  Copy every walked
+ * line's assembled ln g (l = ell_min..ell_max, ragged, in
  * order of l) into out; offsets (length lines+1, may be NULL) receives the
  * start of each line.  *n_out = total bins.  cap too small: WL_EINVAL. */
 wl_status wl_get_surface(wl_handle h, double* out, size_t cap, int64_t* offsets,
                          size_t offsets_cap, size_t* n_out);
 
-/* Counters and timings of the handle (wl_stats above) into *out. */
+/* Counters and timings of the handle (wl_stats above) into *out: moves,
+ * accepted proposals (Eq. 3), flatness checks and stages (Eq. 4) of the walk;
+ * the timings have no paper counterpart.  Errors: WL_EINVAL, WL_ECUDA. */
 wl_status wl_get_stats(wl_handle h, wl_stats* out);
 
 /* Thermodynamics from the assembled surface (the partition function of Eq. 2
@@ -158,7 +186,9 @@ wl_status wl_get_stats(wl_handle h, wl_stats* out);
  * Needs wl_assemble over every line l = 0..N/2 (else WL_ESTATE).  FP64. */
 wl_status wl_thermo(wl_handle h, const double* T, int nT, const double* H, int nH, double* out);
 
-/* Full state of one line walker, in plain layouts: scal[8] = {k, t, F (ln f
+/* The walker of one line as the method section defines it (current k, the
+ * up/down lists the exchange move draws from, ln g, histogram, ln f).
+ * Full state of one line walker, in plain layouts: scal[8] = {k, t, F (ln f
  * in units of u), stage, accepts, t at stage start, status (0 running,
  * 1 converged, 2 overflow), flatness checks}; perm[N] = up-spin list in
  * entries [0, l) followed by the down-spin list; spins[N] = 0/1 per site;
@@ -166,13 +196,17 @@ wl_status wl_thermo(wl_handle h, const double* T, int nT, const double* H, int n
 wl_status wl_get_line_state(wl_handle h, int ell, int64_t* scal, int32_t* perm,
                             uint8_t* spins, int64_t* lng, int64_t* hist, uint8_t* visited);
 
-/* The device-built exp threshold table of the last run (4096 entries:
+/* The deterministic form of Eq. 3's acceptance: the device-built exp
+ * threshold table of the last run (4096 entries:
  * round(2^32 exp(-(i 2^q) u)), q the smallest shift with 4095*2^q*u >=
  * 32 ln 2) and its q.  Errors: WL_ESTATE before the first wl_run. */
 wl_status wl_get_exp_table(wl_handle h, uint64_t* table, int* q);
 
-/* Run the library's device Philox4x32-10 on n counters: out[4i..4i+3] =
- * Philox(ctr[4i..4i+3], key[2i..2i+1]).  Host arrays.  For verification. */
+/* The random numbers of the walk (the paper does not name a generator; this
+ * library uses Philox4x32-10 keyed by (l, seed), counter = move number).
+ * Run the library's device Philox4x32-10 on n counters: out[4i..4i+3] =
+ * Philox(ctr[4i..4i+3], key[2i..2i+1]).  Host arrays.  For verification.
+ * Errors: WL_EINVAL, WL_ECUDA. */
 wl_status wl_philox(size_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out);
 
 /* The walker's form of Eq. 3 for n random words r[i] (the third Philox word of
@@ -186,10 +220,35 @@ wl_status wl_philox(size_t n, const uint32_t* ctr, const uint32_t* key, uint32_t
 wl_status wl_accept_threshold(double ln_f_min, int deterministic, size_t n, const uint32_t* r,
                               int64_t* out);
 
-/* Free the handle's device memory and the handle; h is invalid afterwards. */
+/* Hardware rates the walk's roofline is stated against, measured by the
+ * library's own microbenchmarks on the current device (all SMs busy, many
+ * independent operations in flight per thread): random 4-byte reads from
+ * shared memory, random 32-byte sectors from L2 (32 MB buffer) and from HBM
+ * (4 GB buffer), and lane operations per second of three integer classes.
+ * The walk of Eq. 3 is random access plus integer arithmetic (one Philox
+ * block, list and spin reads, one ln g read per move attempt); the paper has
+ * no counterpart.  Allocates 4 GB of device memory for the duration of the
+ * call.  Errors: WL_EINVAL, WL_ECUDA. */
+typedef struct {
+    double smem_words_per_s;     /* random 4-byte shared-memory reads          */
+    double l2_sectors_per_s;     /* random 32-byte sectors, L2-resident buffer */
+    double hbm_sectors_per_s;    /* random 32-byte sectors, 4 GB buffer        */
+    double lop3_ops_per_s;       /* three-input xor                            */
+    double iadd3_ops_per_s;      /* three-input add                            */
+    double imad_ops_per_s;       /* 32-bit multiply-add                        */
+    double mulwide_ops_per_s;    /* 32x32->64 products (hi and lo) with an xor */
+    int32_t sms;                 /* streaming multiprocessors of the device    */
+} wl_peaks;
+
+wl_status wl_measure_peaks(wl_peaks* out);
+
+/* Free the handle's device memory and the handle; h is invalid afterwards.
+ * No paper counterpart.  Errors: WL_EINVAL (NULL handle). */
 wl_status wl_destroy(wl_handle h);
 
 /* ---- Serving: density-of-states requests with continuous batching ----
+ * No paper counterpart: a deployment of the method (each request is the
+ * method's full walk of one lattice, wl_run + wl_assemble).
  * A server owns a scheduler thread on the device current at creation.
  * Requests (one lattice each, walked as wl_run would, to ln_f_min or to
  * move_budget) are admitted in arrival order while their device footprint
@@ -274,7 +333,8 @@ wl_status wl_walk_noalloc(wl_lattice lattice, int L, int ell_first, int nlines, 
                           void* perm, uint32_t* spins, int64_t* lng, uint64_t* hist,
                           int64_t* state, int64_t stream);
 
-/* Message of the last failed call on this thread ("" if none). */
+/* Message of the last failed call on this thread ("" if none).  No paper
+ * counterpart. */
 const char* wl_last_error(void);
 
 #ifdef __cplusplus

@@ -29,14 +29,14 @@ LATTICES = {"square": WL_SQUARE, "triangular": WL_TRIANGULAR, "cubic": WL_SIMPLE
 STATUS = {0: "WL_OK", 1: "WL_EINVAL", 2: "WL_ENOMEM", 3: "WL_ECUDA", 4: "WL_ETIMEOUT",
           5: "WL_EABORTED", 6: "WL_ENOTCONVERGED", 7: "WL_EMISMATCH", 8: "WL_ESTATE",
           9: "WL_EOVERFLOW"}
-WL_OK, WL_ENOTCONVERGED, WL_ETIMEOUT, WL_EABORTED = 0, 6, 4, 5
+WL_OK, WL_EINVAL, WL_ENOTCONVERGED, WL_ETIMEOUT, WL_EABORTED = 0, 1, 6, 4, 5
 
 EXPORTED = ["wl_create", "wl_required_bytes", "wl_set_option", "wl_get_option", "wl_run",
             "wl_abort", "wl_reset", "wl_assemble", "wl_get_lng", "wl_get_surface",
             "wl_get_stats", "wl_get_line_state", "wl_get_exp_table", "wl_philox", "wl_accept_threshold", "wl_destroy",
             "wl_last_error", "wl_walk_noalloc", "wl_server_create", "wl_server_submit",
             "wl_server_info", "wl_server_wait", "wl_server_result", "wl_server_release",
-            "wl_server_destroy", "wl_thermo"]
+            "wl_server_destroy", "wl_thermo", "wl_measure_peaks", "wl_select_lines"]
 
 
 class WLError(RuntimeError):
@@ -97,6 +97,8 @@ def lib():
         L.wl_get_exp_table.argtypes = [vp, vp, vp]
         L.wl_philox.argtypes = [sz, vp, vp, vp]
         L.wl_accept_threshold.argtypes = [dbl, i32, sz, vp, vp]
+        L.wl_measure_peaks.argtypes = [vp]
+        L.wl_select_lines.argtypes = [vp, vp, i32]
         L.wl_destroy.argtypes = [vp]
         L.wl_last_error.argtypes = []
         L.wl_last_error.restype = cp
@@ -150,6 +152,20 @@ def wl_accept_threshold(ln_f_min: float, deterministic: int, r: np.ndarray) -> n
     return out
 
 
+class wl_peaks(ctypes.Structure):
+    _fields_ = [("smem_words_per_s", ctypes.c_double), ("l2_sectors_per_s", ctypes.c_double),
+                ("hbm_sectors_per_s", ctypes.c_double), ("lop3_ops_per_s", ctypes.c_double),
+                ("iadd3_ops_per_s", ctypes.c_double), ("imad_ops_per_s", ctypes.c_double),
+                ("mulwide_ops_per_s", ctypes.c_double), ("sms", ctypes.c_int32)]
+
+
+def wl_measure_peaks() -> dict:
+    """Random-access and integer-issue rates of the current device (wl.h)."""
+    p = wl_peaks()
+    _check(lib().wl_measure_peaks(ctypes.byref(p)), "wl_measure_peaks")
+    return {k: getattr(p, k) for k, _ in wl_peaks._fields_}
+
+
 class Handle:
     """One lattice's set of micromagnetic-line walkers on the GPU."""
 
@@ -193,6 +209,12 @@ class Handle:
     def run(self, ln_f_min: float, flatness: float = 0.8, allow=(WL_OK, WL_ENOTCONVERGED)) -> int:
         """wl_run; returns the status (WL_OK or WL_ENOTCONVERGED by default)."""
         return _check(lib().wl_run(self._h, ln_f_min, flatness), "wl_run", ok=allow)
+
+    def select_lines(self, ells):
+        """Walk only these lines (wl_select_lines); an empty list restores all."""
+        a = np.ascontiguousarray(list(ells), dtype=np.int32)
+        _check(lib().wl_select_lines(self._h, _p(a) if a.size else None, int(a.size)),
+               "wl_select_lines")
 
     def abort(self):
         _check(lib().wl_abort(self._h), "wl_abort")

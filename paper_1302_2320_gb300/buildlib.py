@@ -20,7 +20,7 @@ LIB = os.path.join(OUT_DIR, "libwl.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["wl_api.cu", "wl_kernels.cu", "wl_walk_square.cu", "wl_walk_square_p2.cu",
            "wl_walk_triangular.cu", "wl_walk_cubic.cu", "wl_noalloc.cu",
-           "wl_server.cu", "wl_walk_square_open.cu"]
+           "wl_server.cu", "wl_walk_square_open.cu", "wl_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
          "-ffp-contract=off", "-I" + INCLUDE]

@@ -247,7 +247,8 @@ Geo make_geo(const wl_ctx* h)
 wl_status upload_queue(wl_ctx* h)
 {
     std::vector<int32_t> order;
-    for (int l = h->ell_min; l <= h->ell_max; ++l) order.push_back(l);
+    for (int l = h->ell_min; l <= h->ell_max; ++l)
+        if (line_selected(h, l)) order.push_back(l);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         return h->lo.desc[a].nbins > h->lo.desc[b].nbins;
     });
@@ -280,8 +281,8 @@ wl_status initialise(wl_ctx* h, double u, int flat_pm)
     if (st) return st;
     CU(cudaMemsetAsync(h->d_flags, 0, 16, h->s));
     CU(cudaMemsetAsync(h->d_st, 0, h->lo.nlines * sizeof(LineState), h->s));
-    // lines outside [ell_min, ell_max] are marked converged with t = 0 so that
-    // no launch touches them
+    // lines outside [ell_min, ell_max], or not in a selected set, are marked
+    // converged with t = 0 so that no launch touches them
     InitArgs a;
     a.g = make_geo(h);
     a.desc = h->d_desc + h->ell_min;
@@ -297,18 +298,24 @@ wl_status initialise(wl_ctx* h, double u, int flat_pm)
     CU(cudaEventRecord(h->ev0, h->s));
     CU(launch_init(h->g.type == WL_SQUARE_OPEN ? (int)kSquareOpen : h->g.type, h->lo.idx16, a, h->s));
     CU(cudaEventRecord(h->ev1, h->s));
-    if (h->ell_min > 0 || h->ell_max < h->lo.nlines - 1) {
+    {
         std::vector<LineState> out(h->lo.nlines);
         for (auto& s : out) {
             memset(&s, 0, sizeof s);
             s.status = 1;
         }
-        CU(cudaMemcpyAsync(h->d_st, out.data(), h->ell_min * sizeof(LineState),
-                           cudaMemcpyHostToDevice, h->s));
-        const int tail = h->lo.nlines - 1 - h->ell_max;
-        if (tail > 0)
-            CU(cudaMemcpyAsync(h->d_st + h->ell_max + 1, out.data(), tail * sizeof(LineState),
+        // runs of lines that are not walked
+        for (int l = 0; l < h->lo.nlines;) {
+            if (line_selected(h, l)) {
+                ++l;
+                continue;
+            }
+            int e = l;
+            while (e < h->lo.nlines && !line_selected(h, e)) ++e;
+            CU(cudaMemcpyAsync(h->d_st + l, out.data(), (size_t)(e - l) * sizeof(LineState),
                                cudaMemcpyHostToDevice, h->s));
+            l = e;
+        }
     }
     CU(cudaStreamSynchronize(h->s));
     float ms = 0;
@@ -607,7 +614,7 @@ wl_status run_plain(wl_ctx* h)
         for (auto st : h->pool) CU(cudaStreamWaitEvent(st, h->ev_join, 0));
         int issued = 0;
         for (int l = h->ell_min; l <= h->ell_max; ++l) {
-            if (st_host[l].status != 0 || st_host[l].t >= h->budget) continue;
+            if (!line_selected(h, l) || st_host[l].status != 0 || st_host[l].t >= h->budget) continue;
             a.order = h->d_ident + l;
             a.qnext = h->d_qheads + l;
             cudaStream_t st = h->pool[issued % npool];
@@ -780,6 +787,7 @@ wl_status wl_set_option(wl_handle h, const char* key, int64_t v)
     } else if (k == "ell_min" || k == "ell_max") {
         if (v < 0 || v >= h->lo.nlines) return fail(WL_EINVAL, "%s must be in [0, %d]", key, h->lo.nlines - 1);
         (k == "ell_min" ? h->ell_min : h->ell_max) = (int)v;
+        h->sel.clear();
     } else {
         return fail(WL_EINVAL, "unknown option '%s'", key);
     }
@@ -823,6 +831,32 @@ wl_status wl_reset(wl_handle h)
     return WL_OK;
 }
 
+wl_status wl_select_lines(wl_handle h, const int32_t* ells, int n)
+{
+    if (!valid_handle(h)) return fail(WL_EINVAL, "NULL handle");
+    if (h->initialized) return fail(WL_ESTATE, "the line set changes the walk; call wl_reset first");
+    if (n < 0 || (n > 0 && !ells)) return fail(WL_EINVAL, "bad line list");
+    if (n == 0) {
+        h->sel.clear();
+        h->ell_min = 0;
+        h->ell_max = h->lo.nlines - 1;
+        return WL_OK;
+    }
+    std::vector<uint8_t> sel(h->lo.nlines, 0);
+    int lo = h->lo.nlines, hi = -1;
+    for (int x = 0; x < n; ++x) {
+        const int l = ells[x];
+        if (l < 0 || l >= h->lo.nlines) return fail(WL_EINVAL, "line %d outside [0, %d]", l, h->lo.nlines - 1);
+        sel[l] = 1;
+        lo = std::min(lo, l);
+        hi = std::max(hi, l);
+    }
+    h->sel.swap(sel);
+    h->ell_min = lo;
+    h->ell_max = hi;
+    return WL_OK;
+}
+
 wl_status wl_abort(wl_handle h)
 {
     if (!valid_handle(h)) return fail(WL_EINVAL, "NULL handle");
@@ -853,7 +887,8 @@ wl_status wl_run(wl_handle h, double ln_f_min, double flatness)
     if (st) return st;
     if (e != cudaSuccess) return fail(WL_ECUDA, "run failed: %s", cudaGetErrorString(e));
     const Summary sm = *h->h_summary;
-    const int selected = h->ell_max - h->ell_min + 1;
+    int selected = 0;
+    for (int l = h->ell_min; l <= h->ell_max; ++l) selected += line_selected(h, l);
     const int outside = h->lo.nlines - selected;
     if (sm.converged - outside < selected) return fail(WL_ENOTCONVERGED, "move budget reached before convergence");
     g_err.clear();
@@ -891,7 +926,7 @@ wl_status wl_get_lng(wl_handle h, int ell, double* out, size_t cap, int* k_lo, i
     if (ell < 0 || ell > h->g.N) return fail(WL_EINVAL, "ell out of range");
     if (!h->assembled) return fail(WL_ESTATE, "call wl_assemble first");
     const int li = std::min(ell, h->g.N - ell);
-    if (li < h->ell_min || li > h->ell_max) return fail(WL_EINVAL, "line %d was not walked", ell);
+    if (!line_selected(h, li)) return fail(WL_EINVAL, "line %d was not walked", ell);
     const LineDesc& d = h->lo.desc[li];
     if (n_out) *n_out = (size_t)d.nbins;
     if (k_lo) *k_lo = 0;
@@ -927,7 +962,7 @@ wl_status wl_get_stats(wl_handle h, wl_stats* out)
 {
     if (!valid_handle(h) || !out) return fail(WL_EINVAL, "NULL argument");
     memset(out, 0, sizeof *out);
-    out->lines = h->ell_max - h->ell_min + 1;
+    for (int l = h->ell_min; l <= h->ell_max; ++l) out->lines += line_selected(h, l);
     out->mapping = h->last_mapping;
     out->form = h->form;
     out->launches = h->launches;
@@ -940,6 +975,7 @@ wl_status wl_get_stats(wl_handle h, wl_stats* out)
     CU(cudaStreamSynchronize(h->s));
     out->min_stage = INT32_MAX;
     for (int l = h->ell_min; l <= h->ell_max; ++l) {
+        if (!line_selected(h, l)) continue;
         const LineState& s = st[l];
         out->moves += s.t;
         out->accepts += s.accepts;
@@ -1004,7 +1040,7 @@ wl_status wl_thermo(wl_handle h, const double* T, int nT, const double* H, int n
 {
     if (!valid_handle(h) || !T || !H || !out || nT < 1 || nH < 1) return fail(WL_EINVAL, "bad arguments");
     if (!h->assembled) return fail(WL_ESTATE, "call wl_assemble first");
-    if (h->ell_min != 0 || h->ell_max != h->lo.nlines - 1)
+    if (h->ell_min != 0 || h->ell_max != h->lo.nlines - 1 || !h->sel.empty())
         return fail(WL_ESTATE, "thermodynamics needs every line l = 0..N/2");
     for (int a = 0; a < nT; ++a)
         if (!(T[a] > 0.0)) return fail(WL_EINVAL, "temperatures must be > 0");

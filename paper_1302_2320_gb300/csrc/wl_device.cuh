@@ -20,9 +20,10 @@ constexpr int kTableBytes = kTableN * 4;     // entries 1..4095 as u32; entry 0 
 // fewer neighbours; k takes every value, so bins have step 1).
 enum LatticeType : int { kSquare = 0, kTriangular = 1, kCubic = 2, kSquareP2 = 3, kSquareOpen = 4 };
 
-// Per-walker window of ln g (int64) and histogram (u64) bins in shared memory.
+// Per-walker window in shared memory: ln g (int64) of kWin bins, then the
+// histogram counts (u32) the walker added to them since the window was loaded.
 constexpr int kWin = 64;
-constexpr int kWinBytes = kWin * 16;
+constexpr int kWinBytes = kWin * 12;
 
 // Per-line scalar state (device, one per walked line).
 struct LineState {
@@ -220,39 +221,82 @@ __device__ __forceinline__ int delta_k_nb(const Geo& g, const uint32_t* sp, uint
 // by integer comparisons, so the result never depends on the estimate.
 __device__ __forceinline__ uint64_t table_at(const uint32_t* tab, int i)
 {
-    return i == 0 ? (1ull << 32) : (uint64_t)__ldg(tab + i);
+    return i == 0 ? (1ull << 32) : (uint64_t)tab[i];
+}
+
+// Rare path of dmax_det: the segment by bisection (t[lo] > r >= t[hi]).
+static __device__ __noinline__ int dmax_segment_search(uint32_t r, const uint32_t* tab)
+{
+    int lo = 0, hi = kTableN - 1;
+    if (table_at(tab, hi - 1) > (uint64_t)r) return hi - 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (table_at(tab, mid) > (uint64_t)r) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Integer <-> float conversions by bit manipulation (the 64-bit conversion
+// instructions run on the FP64 pipe, which is slow on this GPU).
+// u64 -> float, mantissa truncated (relative error below 2^-23).
+__device__ __forceinline__ float u64_to_float_rz(uint64_t x)
+{
+    if (x == 0) return 0.0f;
+    const int lz = __clzll((long long)x);
+    const uint32_t m = (uint32_t)((x << lz) >> 40);          // 24 bits, top bit set
+    return __uint_as_float(((uint32_t)(190 - lz) << 23) | (m & 0x7FFFFFu));
+}
+
+// floor of a float in [0, 2^62]
+__device__ __forceinline__ int64_t float_floor_i64(float f)
+{
+    const uint32_t bits = __float_as_uint(f);
+    const int e = (int)(bits >> 23) - 127;                   // f = 1.m * 2^e
+    if (e < 0) return 0;
+    const uint64_t m = (bits & 0x7FFFFFu) | 0x800000u;
+    return e >= 23 ? (int64_t)(m << (e - 23)) : (int64_t)(m >> (23 - e));
 }
 
 __device__ __forceinline__ int64_t dmax_det(uint32_t r, const uint32_t* tab, int q, float seg_per_log2)
 {
-    // t[i] ~ 2^32 * 2^(-i / seg_per_log2)  =>  i ~ (32 - log2 r) * seg_per_log2
-    int c = __float2int_rd((32.0f - __log2f((float)r + 0.5f)) * seg_per_log2);
-    c = c < 0 ? 0 : (c > kTableN - 2 ? kTableN - 2 : c);
-    uint64_t t0 = table_at(tab, c), t1 = table_at(tab, c + 1);
-    // i* = max{i <= 4094 : t[i] > r}; t is non-increasing
-    while (t0 <= (uint64_t)r) {               // too far right (c > 0 here: t[0] > r)
-        --c;
-        t1 = t0;
-        t0 = table_at(tab, c);
+    // t[i] ~ 2^32 * 2^(-i / seg_per_log2)  =>  i* ~ (32 - log2 r) * seg_per_log2;
+    // the segment is one of c-1, c, c+1 unless r is tiny (the table's flat tail)
+    const uint32_t r1 = r | 1u;
+    const int lz = __clz(r1);
+    const uint32_t frac = (uint32_t)(((uint64_t)r1 << (lz + 1)) >> 9) & 0x7FFFFFu;   // bits below the leading one
+    const float lr = __log2f(__uint_as_float(0x3F800000u | frac)) + (float)(31 - lz);
+    int c = (int)float_floor_i64(fmaxf((32.0f - lr) * seg_per_log2, 0.0f));
+    c = c < 1 ? 1 : (c > kTableN - 3 ? kTableN - 3 : c);
+    const uint64_t R = r;
+    const uint64_t tm = table_at(tab, c - 1), t0 = (uint64_t)tab[c], t1 = (uint64_t)tab[c + 1],
+                   t2 = (uint64_t)tab[c + 2];
+    // i* = max{i <= 4094 : t[i] > r}, t non-increasing
+    int seg;
+    uint64_t a, b;                  // t[i*], t[i*+1]
+    if (t0 > R && t1 <= R) {
+        seg = c; a = t0; b = t1;
+    } else if (tm > R && t0 <= R) {
+        seg = c - 1; a = tm; b = t0;
+    } else if (t1 > R && (t2 <= R || c + 1 == kTableN - 2)) {
+        seg = c + 1; a = t1; b = t2;
+    } else {
+        seg = dmax_segment_search(r, tab);
+        a = table_at(tab, seg);
+        b = table_at(tab, seg + 1);
     }
-    while (c < kTableN - 2 && t1 > (uint64_t)r) {   // too far left
-        ++c;
-        t0 = t1;
-        t1 = table_at(tab, c + 1);
-    }
-    if (t1 > (uint64_t)r) return ((int64_t)(kTableN - 1) << q) - 1;   // whole last segment
+    if (b > R) return ((int64_t)(kTableN - 1) << q) - 1;   // the whole last segment
     // largest frac < 2^q with diff * frac < X 2^q, i.e. floor((X 2^q - 1) / diff)
-    const uint64_t X = t0 - (uint64_t)r;          // 1 .. diff
-    const uint64_t diff = t0 - t1;
+    const uint64_t X = a - R;                 // 1 .. diff
+    const uint32_t diff = (uint32_t)(a - b);  // < 2^32
     const uint64_t num = (X << q) - 1ull;
-    const float rd = __frcp_rn((float)diff);
-    int64_t fr = (int64_t)((float)num * rd);
-    // one refinement of the float quotient by its integer residual, then exact steps
-    fr += (int64_t)((float)((int64_t)num - (int64_t)(diff * (uint64_t)fr)) * rd);
-    if (fr < 0) fr = 0;
-    while (fr > 0 && diff * (uint64_t)fr > num) --fr;
-    while (diff * (uint64_t)(fr + 1) <= num) ++fr;
-    return ((int64_t)c << q) + fr;
+    float rd;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rd) : "f"(u64_to_float_rz(diff)));
+    int64_t fr = float_floor_i64(u64_to_float_rz(num) * rd);
+    // the float quotient is within a unit or two up to q = 22; exact steps finish it
+    while (fr > 0 && (uint64_t)diff * (uint64_t)fr > num) --fr;
+    while ((uint64_t)diff * (uint64_t)(fr + 1) <= num) ++fr;
+    return ((int64_t)seg << q) + fr;
 }
 
 // Production rule: accept iff U < exp(-u d), U = (r/2^8 + 1/2) 2^-24 in (0, 1),
@@ -263,8 +307,7 @@ __device__ __forceinline__ int64_t dmax_prod(uint32_t r, float inv_u)
     const uint32_t mm = r >> 8;
     const float nl = mm >= (1u << 23) ? -log1pf(-((float)((1u << 24) - mm) - 0.5f) * 0x1p-24f)
                                       : -__logf(((float)mm + 0.5f) * 0x1p-24f);
-    const float bound = nl * inv_u;
-    return bound >= 0x1p62f ? ((int64_t)1 << 62) : (int64_t)bound;
+    return float_floor_i64(fminf(nl * inv_u, 0x1p62f));
 }
 
 // The random numbers of one move attempt, drawn ahead of the walk: list slots

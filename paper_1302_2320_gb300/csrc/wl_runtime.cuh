@@ -52,6 +52,7 @@ struct wl_ctx {
     int64_t timeout_ms = 0;
     int64_t hbm_budget = 0;
     int ell_min = 0, ell_max = 0;
+    std::vector<uint8_t> sel;   // lines chosen by wl_select_lines (empty: every line in [ell_min, ell_max])
     int same_f_resets = 0;
     // state
     bool allocated = false, initialized = false, assembled = false;
@@ -97,6 +98,12 @@ struct wl_ctx {
 
 namespace wl {
 void set_last_error(const char* msg);   // the message wl_last_error() returns
+
+// Line l is walked: inside [ell_min, ell_max] and, if a set was selected, in it.
+inline bool line_selected(const wl_ctx* h, int l)
+{
+    return l >= h->ell_min && l <= h->ell_max && (h->sel.empty() || h->sel[l]);
+}
 
 namespace rt {
 

@@ -18,7 +18,7 @@
 //     bin or the proposals.
 // An accepted exchange of (i_e, j_e) changes a later proposal in two ways.  If
 // the proposal reuses list slot a_e or b_e its sites are no longer U[a], D[b]:
-// the batch ends there.  If one of i_e, j_e neighbours its sites, its change of
+// the batch is cut short before it.  If one of i_e, j_e neighbours its sites, its change of
 // k is off by 2 for every such neighbour (i_e turned down, j_e up): the later
 // lanes correct it in place and are tested again.  The exchanges accepted in a
 // batch touch distinct slots and distinct sites, so they are applied together
@@ -27,9 +27,10 @@
 // flatness check (t multiple of C) or the end of the slice.
 //
 // The current bin's ln g and its visits not yet counted live in registers; the
-// bins around it live in a shared-memory window (ln g, and histogram counts
-// added by one lane when the walker leaves a bin), written back when the
-// walker re-centres it, at every check and at the end.
+// bins around it live in a shared-memory window (ln g, and the histogram counts
+// added since the window was loaded, by one lane when the walker leaves a
+// bin), written back when the walker re-centres it, at every check and at the
+// end.
 #pragma once
 
 #include "wl_device.cuh"
@@ -103,32 +104,35 @@ __device__ void group_stage_step(int64_t* lng, hist_t* hist, int nbins, int m, u
 // Window of ln g / histogram bins a walker keeps in shared memory.  Every
 // proposal lies within z bins of the current bin (|dk| <= 2z), so the window
 // [wb, wb + kWin) is re-centred whenever the current bin comes within z bins of
-// an edge that is not the line's own edge.  Histogram words in the window gain
-// counts only; a bin with a count is marked visited when the window is stored.
-// Counts reaching 2^62 (far beyond any run) are reported as an overflow.
+// an edge that is not the line's own edge.  The window holds ln g and the
+// counts added since it was loaded; storing it adds the counts to the global
+// histogram (a bin with a count is marked visited) and zeroes them.  Counts
+// reaching 2^62 (far beyond any run) are reported as an overflow.
 template <int S>
-__device__ __forceinline__ bool window_store(int64_t* wl, hist_t* wh, int64_t* lng, hist_t* hist,
+__device__ __forceinline__ bool window_store(int64_t* wl, uint32_t* wd, int64_t* lng, hist_t* hist,
                                              int wb, int wn, int m)
 {
     bool ovf = false;
     for (int x = m; x < wn; x += S) {
-        hist_t h = wh[x];
-        const hist_t cnt = h & ~kVisited;
-        if (cnt) h |= kVisited;
-        ovf |= cnt >= (1ull << 62);
         lng[wb + x] = wl[x];
-        hist[wb + x] = h;
+        const uint32_t add = wd[x];
+        if (add) {
+            const hist_t h = hist[wb + x] + add;
+            ovf |= (h & ~kVisited) >= (1ull << 62);
+            hist[wb + x] = h | kVisited;
+            wd[x] = 0u;
+        }
     }
     return ovf;
 }
 
 template <int S>
-__device__ __forceinline__ void window_load(int64_t* wl, hist_t* wh, const int64_t* lng,
-                                            const hist_t* hist, int wb, int wn, int m)
+__device__ __forceinline__ void window_load(int64_t* wl, uint32_t* wd, const int64_t* lng, int wb,
+                                            int wn, int m)
 {
     for (int x = m; x < wn; x += S) {
         wl[x] = lng[wb + x];
-        wh[x] = hist[wb + x];
+        wd[x] = 0u;
     }
 }
 
@@ -163,7 +167,7 @@ __device__ __forceinline__ Draw shfl_draw(unsigned gmask, const Draw& d, int src
 
 // Walk line `li` for up to A.slice_moves moves (or to its budget, or to
 // convergence).  perm/sp point at the line's list and spins (shared or global
-// memory); win is the group's window (kWin int64 ln g, then kWin u64 hist).
+// memory); win is the group's window (kWin int64 ln g, then kWin u32 counts).
 // All lanes of the group hold identical copies of the scalar state.
 //
 // Draws are double-buffered: lane m holds the draw of step t + m in d0 and of
@@ -178,6 +182,7 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
     constexpr int zb = Coord<LAT>::zbin;  // largest bin step of one move
     constexpr int ks = Coord<LAT>::kshift;
     constexpr int zc = Coord<LAT>::z;
+    constexpr bool kPack = sizeof(IDX) == 2;   // slots and sites fit 16 bits
     const LineDesc D = A.desc[li];
     LineState* P = A.st + li;
     int64_t t = P->t, F = P->F, stage = P->stage, accepts = P->accepts;
@@ -190,7 +195,7 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
     int64_t* lng = A.lng + D.bin_off;
     hist_t* hist = A.hist + D.bin_off;
     int64_t* wl = reinterpret_cast<int64_t*>(win);
-    hist_t* wh = reinterpret_cast<hist_t*>(win + kWin * 8);
+    uint32_t* wd = reinterpret_cast<uint32_t*>(win + kWin * 8);
     const uint2 key = make_uint2((uint32_t)ell, A.seed);
     int64_t end = t + A.slice_moves;
     if (end > A.budget) end = A.budget;
@@ -198,7 +203,7 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
     int bc = k >> ks;
     int wb = window_base(bc, nbins);
     const int wn = nbins < kWin ? nbins : kWin;
-    window_load<S>(wl, wh, lng, hist, wb, wn, m);
+    window_load<S>(wl, wd, lng, wb, wn, m);
     __syncwarp(gmask);
     int64_t cur = wl[bc - wb];    // ln g of the current bin, every visit included
     int pend = 0;                 // visits to the current bin not yet in the window
@@ -229,81 +234,94 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
             // accepted iff ln g(target) <= ln g(current before step m) + dmax, and
             // ln g(current before step m) = u + m F while the walker keeps its bin
             const int64_t base = mF + d0.dmax;
+            const uint32_t ab = kPack ? (a | (b << 16)) : a;
+            const uint32_t ij = kPack ? (i | (j << 16)) : i;
             // -- resolve
-            const unsigned live = lim >= 32 ? 0xffffffffu : ((1u << lim) - 1u);
+            int lim_eff = lim;                                   // cut short by a reused slot
+            unsigned live = lim >= 32 ? 0xffffffffu : ((1u << lim) - 1u);
+            unsigned done = 0u;                                  // steps resolved so far
             int64_t u = cur;      // ln g of the current bin before step 0, shifted as above
             int ent = -pend;      // batch step at which the walker entered its bin
-            unsigned inv = 0u, accm = 0u, evb = 0u;
-            int e0 = 0, c = lim;
+            unsigned accm = 0u, evb = 0u;
+            int c = 0;
             bool eval = true;
-            int pk = 0;           // (dk + 64) << 1 | target outside the window
+            int pk = 0;           // dk + 64, bit 7: target outside the window
             int64_t v = 0;        // ln g of the target bin - m F
             for (;;) {
                 if (eval) {
                     // a target outside the window reads the current bin's slot
                     // (always inside) and ends the batch if it is reached
-                    const int bp = (k + dk) >> ks;
-                    const int wx = bp - wb;
+                    const int wx = ((k + dk) >> ks) - wb;
                     const bool off = (unsigned)wx >= (unsigned)wn;
                     const int64_t ld = wl[off ? bc - wb : wx];
-                    const bool acc = dk == 0 || (!off && ld <= u + base);
-                    pk = ((dk + 64) << 1) | (int)off;
+                    const bool acc = (dk == 0) | (ld <= u + base);
+                    pk = (dk + 64) | ((int)off << 7);
                     v = ld - mF;
-                    evb = group_ballot<S>(gmask, gbase, acc || off);
+                    evb = group_ballot<S>(gmask, gbase, acc | off);
                     eval = false;
                 }
-                const unsigned ev = (evb | inv) & live & ~((1u << e0) - 1u);
-                if (ev == 0u) break;                 // steps e0 .. lim-1 rejected
-                const int e = __ffs(ev) - 1;
-                if ((inv >> e) & 1u) {               // reuses a slot of an accepted exchange
-                    c = e;
+                const unsigned ev = evb & live & ~done;
+                if (ev == 0u) {                      // the rest of the batch is rejected
+                    c = lim_eff;
                     break;
                 }
+                const int e = __ffs(ev) - 1;
                 const int src = gbase + e;
                 const int pke = __shfl_sync(gmask, pk, src);
-                const int dke = (pke >> 1) - 64;
-                if (pke & 1) {                       // walked off the window
+                const int dke = (pke & 127) - 64;
+                if (pke & 128) {                     // walked off the window
                     if ((unsigned)((k + dke) >> ks) >= (unsigned)nbins) stop = 4;   // invariant broken
                     c = e;
                     break;
                 }
                 const int64_t ve = __shfl_sync(gmask, v, src);
-                const uint32_t ae = __shfl_sync(gmask, a, src), be = __shfl_sync(gmask, b, src);
-                const uint32_t ie = __shfl_sync(gmask, i, src), je = __shfl_sync(gmask, j, src);
+                const uint32_t abe = __shfl_sync(gmask, ab, src), ije = __shfl_sync(gmask, ij, src);
+                uint32_t be = 0, je = 0;
+                if constexpr (!kPack) {
+                    be = __shfl_sync(gmask, b, src);
+                    je = __shfl_sync(gmask, j, src);
+                }
                 accm |= 1u << e;
+                done = (2u << e) - 1u;
                 if (dke != 0) {
                     // leave the current bin: steps e0 .. e-1 were rejections in it
                     wl[bc - wb] = u + (int64_t)e * F;
-                    if (m == 0) atomicAdd(reinterpret_cast<unsigned long long*>(wh + (bc - wb)),
-                                          (unsigned long long)(e - ent));
+                    if (m == 0) atomicAdd(wd + (bc - wb), (uint32_t)(e - ent));
                     k += dke;
                     bc = k >> ks;
                     u = ve;
                     ent = e;
                     eval = true;
                 }
-                if (e + 1 < lim) {
-                    // later proposals: a reused slot ends the batch there, a
-                    // neighbouring exchange shifts their change of k
-                    const bool later = m > e;
-                    const bool slot = (a == ae) | (b == be);
-                    bool nbh = false;
+                // later proposals: one that reuses a slot of the exchange cuts the
+                // batch short before it, one next to it gets its change of k shifted
+                const uint32_t ie = kPack ? (ije & 0xFFFFu) : ije;
+                if constexpr (kPack) je = ije >> 16;
+                const uint32_t xs = ab ^ abe;
+                const bool slot = kPack ? (((xs & 0xFFFFu) == 0u) | ((xs >> 16) == 0u))
+                                        : ((xs == 0u) | (b == be));
+                bool nbh = false;
+#pragma unroll
+                for (int q = 0; q < zc; ++q)
+                    nbh |= (ni[q] == ie) | (ni[q] == je) | (nj[q] == ie) | (nj[q] == je);
+                if (group_ballot<S>(gmask, gbase, slot | nbh) & live & ~done) {
+                    const unsigned sm = group_ballot<S>(gmask, gbase, slot) & live & ~done;
+                    if (sm) {
+                        lim_eff = __ffs(sm) - 1;             // > e
+                        live = (1u << lim_eff) - 1u;
+                    }
+                    int cor = 0;
 #pragma unroll
                     for (int q = 0; q < zc; ++q)
-                        nbh |= (ni[q] == ie) | (ni[q] == je) | (nj[q] == ie) | (nj[q] == je);
-                    inv |= group_ballot<S>(gmask, gbase, later && slot);
-                    if (group_ballot<S>(gmask, gbase, later && nbh)) {
-                        int cor = 0;
-#pragma unroll
-                        for (int q = 0; q < zc; ++q)
-                            cor += (int)(nj[q] == ie) - (int)(ni[q] == ie) + (int)(ni[q] == je) -
-                                   (int)(nj[q] == je);
-                        dk += 2 * cor;
-                        eval = true;
-                    }
+                        cor += (int)(nj[q] == ie) - (int)(ni[q] == ie) + (int)(ni[q] == je) -
+                               (int)(nj[q] == je);
+                    dk += 2 * cor;
+                    eval = true;
                 }
-                e0 = e + 1;
-                if (e0 >= lim) break;
+                if ((live & ~done) == 0u) {
+                    c = lim_eff;
+                    break;
+                }
             }
             cur = u + (int64_t)c * F;
             pend = c - ent;
@@ -319,10 +337,10 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
             __syncwarp(gmask);
             if ((bc - zb < wb && wb > 0) || (bc + zb >= wb + kWin && wb + kWin < nbins)) {
                 // re-centre the window (the current bin stays in registers)
-                if (group_ballot<S>(gmask, gbase, window_store<S>(wl, wh, lng, hist, wb, wn, m))) stop = 2;
+                if (group_ballot<S>(gmask, gbase, window_store<S>(wl, wd, lng, hist, wb, wn, m))) stop = 2;
                 __syncwarp(gmask);
                 wb = window_base(bc, nbins);
-                window_load<S>(wl, wh, lng, hist, wb, wn, m);
+                window_load<S>(wl, wd, lng, wb, wn, m);
                 __syncwarp(gmask);
             }
             // shift the draw buffers by c: lane m now needs steps t + c + m (d0)
@@ -352,11 +370,11 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
             __syncwarp(gmask);
             if (m == 0) {
                 wl[bc - wb] = cur;
-                wh[bc - wb] += (hist_t)pend;
+                wd[bc - wb] += (uint32_t)pend;
             }
             pend = 0;
             __syncwarp(gmask);
-            if (group_ballot<S>(gmask, gbase, window_store<S>(wl, wh, lng, hist, wb, wn, m))) {
+            if (group_ballot<S>(gmask, gbase, window_store<S>(wl, wd, lng, hist, wb, wn, m))) {
                 stop = 2;
                 break;
             }
@@ -367,7 +385,7 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
                 // extra reset at unchanged f within the first R checks of a
                 // stage (the remark after Eq. 4): histogram reset, ln g shifted
                 group_stage_step<S>(lng, hist, nbins, m, gmask);
-                window_load<S>(wl, wh, lng, hist, wb, wn, m);
+                window_load<S>(wl, wd, lng, wb, wn, m);
                 __syncwarp(gmask);
                 cur = wl[bc - wb];
             }
@@ -377,7 +395,7 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
                 mF = (int64_t)m * F;
                 stage += 1;
                 t_stage = t;
-                window_load<S>(wl, wh, lng, hist, wb, wn, m);
+                window_load<S>(wl, wd, lng, wb, wn, m);
                 __syncwarp(gmask);
                 cur = wl[bc - wb];
                 if (F == 0) {                // ln f < ln f_min
@@ -401,10 +419,10 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
         __syncwarp(gmask);
         if (m == 0) {
             wl[bc - wb] = cur;
-            wh[bc - wb] += (hist_t)pend;
+            wd[bc - wb] += (uint32_t)pend;
         }
         __syncwarp(gmask);
-        if (group_ballot<S>(gmask, gbase, window_store<S>(wl, wh, lng, hist, wb, wn, m)) && stop == 0)
+        if (group_ballot<S>(gmask, gbase, window_store<S>(wl, wd, lng, hist, wb, wn, m)) && stop == 0)
             stop = 2;
     }
     if (stop == 2) status = 2;

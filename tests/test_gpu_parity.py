@@ -426,3 +426,31 @@ def test_square_L256_sampled_lines():
     for ell in ells:
         assert_line_equal(h, ell, ref[ell], "L256")
     h.close()
+
+
+def test_line_shards_gather_to_the_full_surface():
+    """One surface split by lines (LPT on bins^2, as the ranks of a multi-GPU
+    run would take it) and walked shard after shard on this GPU: each line's
+    state and the gathered assembled surface equal the single full-surface run
+    bit for bit (deterministic mode)."""
+    from paper_1302_2320_gb300 import shard
+    L, seed, u, C, budget = 10, 4, 1e-6, 700, 150_000
+    full = run_gpu("square", L, seed, u, C, budget, mapping=16)
+    full.assemble()
+    ref_vals, ref_offs = full.get_surface()
+    shares = shard.lpt_partition(shard.handle_costs(full), 3)
+    got = {}
+    for share in shares:
+        h = wl.Handle("square", L, seed=seed, check_interval=C, move_budget=budget, mapping=16)
+        got.update(shard.walk_share(h, share, u))
+        for ell in share:
+            a, b = h.line_state(ell), full.line_state(ell)
+            for key in a:
+                assert np.array_equal(a[key], b[key]), (ell, key)
+        st = h.stats()
+        assert st["lines"] == len(share)
+        h.close()
+    vals, offs = shard.ragged_surface(got, full.lines)
+    assert np.array_equal(offs, ref_offs)
+    assert np.array_equal(vals, ref_vals)
+    full.close()
