@@ -361,8 +361,40 @@ WalkArgs base_args(wl_ctx* h)
 
 int kernel_lattice(const wl_ctx* h);
 
-wl_status persistent_shape(wl_ctx* h, int S, int* blocks_per_sm_out, Shape* sh)
+// Tail shape: when no more lines are running than there are SMs, each gets a
+// block of its own with a conflict filter table (exact when it has N entries).
+bool tail_shape(wl_ctx* h, int S, int active, Shape* sh)
 {
+    if (!h->tail || S != 32 || active < 1 || active > h->num_sms) return false;
+    const size_t isz = h->lo.idx16 ? 2 : 4;
+    const size_t stg = (size_t)h->lo.pstride * isz + (size_t)h->lo.W * 4;
+    const size_t cap = std::min<size_t>(h->max_smem, 220 * 1024);
+    int H = 32;
+    while (H < h->g.N && H < 16384) H <<= 1;
+    size_t tbl = (size_t)2 * H * 4;
+    int stage = (kWinBytes + tbl + stg <= cap && stg <= 64 * 1024) ? 1 : 0;
+    while (kWinBytes + tbl + (stage ? stg : 0) > cap && H > 32) {
+        H >>= 1;
+        tbl = (size_t)2 * H * 4;
+    }
+    const size_t slot = kWinBytes + tbl + (stage ? stg : 0);
+    if (slot > cap) return false;
+    int bps = 0;
+    if (walk_kernel_attrs(kernel_lattice(h), 32, h->det != 0, h->lo.idx16, slot, 32, &bps, true) != cudaSuccess ||
+        bps < 1)
+        return false;
+    sh->grid = dim3(std::min(active, h->num_sms));
+    sh->block = dim3(32);
+    sh->smem = slot;
+    sh->stage = stage;
+    sh->slot = (int)slot;
+    sh->tbl_mask = H - 1;
+    return true;
+}
+
+wl_status persistent_shape(wl_ctx* h, int S, int* blocks_per_sm_out, Shape* sh, int active = -1)
+{
+    if (active >= 0 && !blocks_per_sm_out && tail_shape(h, S, active, sh)) return WL_OK;
     const size_t isz = h->lo.idx16 ? 2 : 4;
     const size_t stg = (size_t)h->lo.pstride * isz + (size_t)h->lo.W * 4;
     const size_t cap = std::min<size_t>(h->max_smem, 220 * 1024);
@@ -422,6 +454,7 @@ wl_status enqueue_slice(wl_ctx* h, int S, const Shape& sh)
     WalkArgs a = base_args(h);
     a.stage_smem = sh.stage;
     a.slot_bytes = sh.slot;
+    a.tbl_mask = sh.tbl_mask;
     CU(cudaMemsetAsync(a.qnext, 0, 4, h->s));
     CU(launch_walk(kernel_lattice(h), S, h->det != 0, h->lo.idx16, sh.grid, sh.block, sh.smem, h->s, a));
     CU(launch_summary(h->d_st, h->lo.nlines, h->budget, h->d_flags, h->d_summary, h->s));
@@ -440,6 +473,7 @@ wl_status run_slice(wl_ctx* h, int S, const Shape& sh, bool use_graph)
     WalkArgs now = base_args(h);
     now.stage_smem = sh.stage;
     now.slot_bytes = sh.slot;
+    now.tbl_mask = sh.tbl_mask;
     const bool same = h->graph && h->graph_S == S && h->graph_stage == sh.stage &&
                       h->graph_grid == sh.grid.x && h->graph_block == sh.block.x &&
                       memcmp(&h->graph_args, &now, sizeof now) == 0;
@@ -520,7 +554,8 @@ wl_status run_persistent(wl_ctx* h, std::chrono::steady_clock::time_point t_star
             h->slice_moves = cand_i < 6 ? std::min<int64_t>(saved_slice, 1 << 16) : saved_slice;
         }
         Shape sh;
-        wl_status st = persistent_shape(h, curS, nullptr, &sh);
+        const int active = prev_moves < 0 ? h->nqueue : h->h_summary->active;
+        wl_status st = persistent_shape(h, curS, nullptr, &sh, tuning && cand_i < 6 ? -1 : active);
         if (st) {
             h->slice_moves = saved_slice;
             return st;
@@ -687,6 +722,21 @@ wl_status summary_status(wl_ctx* h, const Summary& sm) { return check_flags(h, s
 
 size_t handle_bytes(const wl_ctx* h) { return required_bytes(h->g, h->lo); }
 
+wl_status assemble_copy_async(wl_ctx* h, double* dst, size_t cap, size_t* n_out)
+{
+    if (!h->initialized) return fail(WL_ESTATE, "no run to assemble");
+    const LineDesc& a = h->lo.desc[h->ell_min];
+    const LineDesc& b = h->lo.desc[h->ell_max];
+    const size_t n = (size_t)(b.bin_off + b.nbins - a.bin_off);
+    if (n_out) *n_out = n;
+    if (!dst || cap < n) return fail(WL_EINVAL, "output capacity %zu < %zu bins", cap, n);
+    CU(launch_assemble(h->d_desc + h->ell_min, h->d_lng, h->d_hist, h->g.N,
+                       h->ell_max - h->ell_min + 1, h->u, h->d_out, h->s));
+    CU(cudaMemcpyAsync(dst, h->d_out + a.bin_off, n * 8, cudaMemcpyDeviceToHost, h->s));
+    h->assembled = true;
+    return WL_OK;
+}
+
 int table_shift(double u)
 {
     const double need = 32.0 * std::log(2.0);
@@ -784,6 +834,9 @@ wl_status wl_set_option(wl_handle h, const char* key, int64_t v)
     } else if (k == "same_f_resets") {
         if (v < 0 || v > 1000000) return fail(WL_EINVAL, "same_f_resets must be in [0, 10^6]");
         h->same_f_resets = (int)v;
+    } else if (k == "tail") {
+        if (v != 0 && v != 1) return fail(WL_EINVAL, "tail must be 0 or 1");
+        h->tail = (int)v;
     } else if (k == "ell_min" || k == "ell_max") {
         if (v < 0 || v >= h->lo.nlines) return fail(WL_EINVAL, "%s must be in [0, %d]", key, h->lo.nlines - 1);
         (k == "ell_min" ? h->ell_min : h->ell_max) = (int)v;
@@ -810,6 +863,7 @@ wl_status wl_get_option(wl_handle h, const char* key, int64_t* v)
     else if (k == "hbm_budget") *v = h->hbm_budget;
     else if (k == "ell_min") *v = h->ell_min;
     else if (k == "same_f_resets") *v = h->same_f_resets;
+    else if (k == "tail") *v = h->tail;
     else if (k == "ell_max") *v = h->ell_max;
     else if (k == "N") *v = h->g.N;
     else if (k == "NB") *v = h->g.NB;

@@ -507,9 +507,10 @@ cudaError_t launch_walk(int lattice, int S, bool det, bool idx16, dim3 grid, dim
 }
 
 cudaError_t walk_kernel_attrs(int lattice, int S, bool det, bool idx16, size_t smem,
-                              int block_threads, int* blocks_per_sm)
+                              int block_threads, int* blocks_per_sm, bool tbl)
 {
     WalkArgs dummy{};
+    dummy.tbl_mask = tbl ? 1 : 0;
     const dim3 z(0), b(block_threads);
     if (lattice == kSquare) return launch_walk_square(S, det, idx16, z, b, smem, 0, dummy, blocks_per_sm);
     if (lattice == kSquareP2)

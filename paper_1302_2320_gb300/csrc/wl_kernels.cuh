@@ -39,7 +39,7 @@ constexpr int kMappings[] = {1, 2, 4, 8, 16, 32};
 cudaError_t launch_walk(int lattice, int S, bool det, bool idx16, dim3 grid, dim3 block,
                         size_t smem, cudaStream_t s, const WalkArgs& a);
 cudaError_t walk_kernel_attrs(int lattice, int S, bool det, bool idx16, size_t smem,
-                              int block_threads, int* blocks_per_sm);
+                              int block_threads, int* blocks_per_sm, bool tbl = false);
 
 cudaError_t launch_walk_square(int S, bool det, bool idx16, dim3 grid, dim3 block, size_t smem,
                                cudaStream_t s, const WalkArgs& a, int* bps);

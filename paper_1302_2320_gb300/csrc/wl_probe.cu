@@ -78,8 +78,9 @@ __global__ void random_smem_kernel(int iters, uint32_t* out)
 // next value from its own and its neighbour's previous values (so nothing
 // folds at compile time, and the kStreams operations of a round are
 // independent), one operation of the class per chain step.  0: three-input
-// xor (logic), 1: three-input add, 2: 32-bit multiply-add, 3: a 32x32->64
-// product (high and low words) xor-ed with a neighbour, as in a Philox round.
+// logic (and-xor, nonlinear so that rounds cannot be folded), 1: three-input
+// add, 2: 32-bit multiply-add, 3: a 32x32->64 product (high and low words)
+// xor-ed with a neighbour, as in a Philox round.
 template <int KIND>
 __global__ void int_issue_kernel(int iters, uint32_t seed, uint32_t* out)
 {
@@ -94,7 +95,7 @@ __global__ void int_issue_kernel(int iters, uint32_t seed, uint32_t* out)
 #pragma unroll
             for (int s = 0; s < kStreams; ++s) {
                 const uint32_t x = a[s], y = a[(s + 1) % kStreams], k = 0x9E3779B9u * (r + 1);
-                if (KIND == 0) b[s] = x ^ y ^ k;
+                if (KIND == 0) b[s] = (x & y) ^ k;
                 else if (KIND == 1) b[s] = x + y + k;
                 else if (KIND == 2) b[s] = x * y + k;
                 else b[s] = __umulhi(x, 0xD2511F53u) ^ (x * 0xD2511F53u) ^ y;

@@ -31,6 +31,7 @@ struct Shape {
     size_t smem;
     int stage;
     int slot;
+    int tbl_mask = 0;   // tail shape: one walker per block with a conflict filter table
 };
 
 }  // namespace rt
@@ -54,6 +55,7 @@ struct wl_ctx {
     int ell_min = 0, ell_max = 0;
     std::vector<uint8_t> sel;   // lines chosen by wl_select_lines (empty: every line in [ell_min, ell_max])
     int same_f_resets = 0;
+    int tail = 1;            // option "tail": few active lines get the one-walker-per-SM shape
     // state
     bool allocated = false, initialized = false, assembled = false;
     double u = 0.0;
@@ -120,6 +122,10 @@ wl_status launch_slice_async(wl_ctx* h, int S, const Shape& sh);
 wl_status summary_status(wl_ctx* h, const Summary& sm);
 // Device bytes held by a handle of this lattice.
 size_t handle_bytes(const wl_ctx* h);
+// Enqueue the assembly of every walked line (Eq. 4) and the copy of the
+// surface into host memory `dst` (pinned for an asynchronous copy) on the
+// handle's stream; returns without waiting.  n_out = bins copied.
+wl_status assemble_copy_async(wl_ctx* h, double* dst, size_t cap, size_t* n_out);
 // The exp threshold table as built on the host, to check the device-built one:
 // q, the smallest shift with 4095 * 2^q * u >= 32 ln 2 (-1 if none below 40),
 // and entry i, round(2^32 exp(-(i 2^q) u)) evaluated in long double.

@@ -175,9 +175,9 @@ __device__ __forceinline__ Draw shfl_draw(unsigned gmask, const Draw& d, int src
 // plain copy when c = S, the usual case), and the lanes whose entry falls past
 // the buffered range take the draw of step t + c + S + m, computed at the
 // start of the next batch so its latency overlaps that batch's work.
-template <int LAT, int S, bool DET, typename IDX>
+template <int LAT, int S, bool DET, typename IDX, bool TBL>
 __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned gmask,
-                          IDX* perm, uint32_t* sp, uint8_t* win)
+                          IDX* perm, uint32_t* sp, uint8_t* win, uint32_t* tbl)
 {
     constexpr int zb = Coord<LAT>::zbin;  // largest bin step of one move
     constexpr int ks = Coord<LAT>::kshift;
@@ -236,30 +236,44 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
             const int64_t base = mF + d0.dmax;
             const uint32_t ab = kPack ? (a | (b << 16)) : a;
             const uint32_t ij = kPack ? (i | (j << 16)) : i;
-            // -- resolve
+            if constexpr (TBL) {
+                // conflict filter: which lanes have a site among their neighbours
+                // (first half) or a list position (second half), hashed by the
+                // low bits; an accepted exchange looks up its own sites and slots
+                const uint32_t tm = (uint32_t)A.tbl_mask, bit = 1u << m;
+#pragma unroll
+                for (int q = 0; q < zc; ++q) {
+                    atomicOr(&tbl[ni[q] & tm], bit);
+                    atomicOr(&tbl[nj[q] & tm], bit);
+                }
+                atomicOr(&tbl[tm + 1 + (a & tm)], bit);
+                atomicOr(&tbl[tm + 1 + ((ell + b) & tm)], bit);
+                __syncwarp(gmask);
+            }
+            // -- resolve.  One pass of the loop handles one accepted step (an
+            // event): the walker's state is updated by selects, the later lanes
+            // are evaluated again for the next event, and only the rare cases
+            // (off the window, a conflicting later proposal) branch.  Every
+            // branch depends on ballots or on values all lanes hold alike.
             int lim_eff = lim;                                   // cut short by a reused slot
             unsigned live = lim >= 32 ? 0xffffffffu : ((1u << lim) - 1u);
             unsigned done = 0u;                                  // steps resolved so far
             int64_t u = cur;      // ln g of the current bin before step 0, shifted as above
             int ent = -pend;      // batch step at which the walker entered its bin
-            unsigned accm = 0u, evb = 0u;
+            int kw = k - (wb << ks);                             // k relative to the window
+            unsigned accm = 0u;
             int c = 0;
-            bool eval = true;
-            int pk = 0;           // dk + 64, bit 7: target outside the window
-            int64_t v = 0;        // ln g of the target bin - m F
+            int64_t v;            // ln g of the target bin - m F
+            unsigned evb, offb;
+            {
+                const int wx = (kw + dk) >> ks;
+                const bool off = (unsigned)wx >= (unsigned)wn;
+                const int64_t ld = wl[off ? (kw >> ks) : wx];
+                v = ld - mF;
+                evb = group_ballot<S>(gmask, gbase, (dk == 0) | off | (ld <= u + base));
+                offb = group_ballot<S>(gmask, gbase, off);
+            }
             for (;;) {
-                if (eval) {
-                    // a target outside the window reads the current bin's slot
-                    // (always inside) and ends the batch if it is reached
-                    const int wx = ((k + dk) >> ks) - wb;
-                    const bool off = (unsigned)wx >= (unsigned)wn;
-                    const int64_t ld = wl[off ? bc - wb : wx];
-                    const bool acc = (dk == 0) | (ld <= u + base);
-                    pk = (dk + 64) | ((int)off << 7);
-                    v = ld - mF;
-                    evb = group_ballot<S>(gmask, gbase, acc | off);
-                    eval = false;
-                }
                 const unsigned ev = evb & live & ~done;
                 if (ev == 0u) {                      // the rest of the batch is rejected
                     c = lim_eff;
@@ -267,13 +281,7 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
                 }
                 const int e = __ffs(ev) - 1;
                 const int src = gbase + e;
-                const int pke = __shfl_sync(gmask, pk, src);
-                const int dke = (pke & 127) - 64;
-                if (pke & 128) {                     // walked off the window
-                    if ((unsigned)((k + dke) >> ks) >= (unsigned)nbins) stop = 4;   // invariant broken
-                    c = e;
-                    break;
-                }
+                const int dke = __shfl_sync(gmask, dk, src);
                 const int64_t ve = __shfl_sync(gmask, v, src);
                 const uint32_t abe = __shfl_sync(gmask, ab, src), ije = __shfl_sync(gmask, ij, src);
                 uint32_t be = 0, je = 0;
@@ -281,30 +289,60 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
                     be = __shfl_sync(gmask, b, src);
                     je = __shfl_sync(gmask, j, src);
                 }
-                accm |= 1u << e;
-                done = (2u << e) - 1u;
-                if (dke != 0) {
-                    // leave the current bin: steps e0 .. e-1 were rejections in it
-                    wl[bc - wb] = u + (int64_t)e * F;
-                    if (m == 0) atomicAdd(wd + (bc - wb), (uint32_t)(e - ent));
-                    k += dke;
-                    bc = k >> ks;
-                    u = ve;
-                    ent = e;
-                    eval = true;
+                const bool offe = (offb >> e) & 1u;  // walked off the window: ends the batch at e
+                // accepted step e: a new bin means steps e0 .. e-1 were rejections in the old one
+                const bool mv = (dke != 0) & !offe;
+                const int x = kw >> ks;
+                if (mv) {
+                    wl[x] = u + (int64_t)e * F;
+                    wd[x] += (uint32_t)(e - ent);
                 }
+                k = mv ? k + dke : k;
+                kw = mv ? kw + dke : kw;
+                u = mv ? ve : u;
+                ent = mv ? e : ent;
+                accm |= offe ? 0u : (1u << e);
+                done = (2u << e) - 1u;
+                // the later lanes against the new state
+                int wx = (kw + dk) >> ks;
+                bool off = (unsigned)wx >= (unsigned)wn;
+                int64_t ld = wl[off ? (kw >> ks) : wx];
+                bool acc = (dk == 0) | off | (ld <= u + base);
                 // later proposals: one that reuses a slot of the exchange cuts the
                 // batch short before it, one next to it gets its change of k shifted
                 const uint32_t ie = kPack ? (ije & 0xFFFFu) : ije;
                 if constexpr (kPack) je = ije >> 16;
                 const uint32_t xs = ab ^ abe;
-                const bool slot = kPack ? (((xs & 0xFFFFu) == 0u) | ((xs >> 16) == 0u))
-                                        : ((xs == 0u) | (b == be));
-                bool nbh = false;
+                bool conflict;
+                if constexpr (TBL) {
+                    // lanes that may be affected (a superset); tested exactly below
+                    const uint32_t tm = (uint32_t)A.tbl_mask;
+                    const uint32_t ae = kPack ? (abe & 0xFFFFu) : abe;
+                    if constexpr (kPack) be = abe >> 16;
+                    conflict = ((tbl[ie & tm] | tbl[je & tm] | tbl[tm + 1 + (ae & tm)] |
+                                 tbl[tm + 1 + ((ell + be) & tm)]) & live & ~done) != 0u;
+                }
+                bool n0 = false, n1 = false, n2 = false, n3 = false, slot = false;
+                if constexpr (!TBL) {
+                    slot = kPack ? (((xs & 0xFFFFu) == 0u) | ((xs >> 16) == 0u)) : ((xs == 0u) | (b == be));
 #pragma unroll
-                for (int q = 0; q < zc; ++q)
-                    nbh |= (ni[q] == ie) | (ni[q] == je) | (nj[q] == ie) | (nj[q] == je);
-                if (group_ballot<S>(gmask, gbase, slot | nbh) & live & ~done) {
+                    for (int q = 0; q < zc; ++q) {
+                        n0 |= ni[q] == ie;
+                        n1 |= ni[q] == je;
+                        n2 |= nj[q] == ie;
+                        n3 |= nj[q] == je;
+                    }
+                }
+                if (offe) {
+                    if ((unsigned)((k + dke) >> ks) >= (unsigned)nbins) stop = 4;   // invariant broken
+                    c = e;
+                    break;
+                }
+                if constexpr (!TBL)
+                    conflict = (group_ballot<S>(gmask, gbase, slot | (n0 | n1) | (n2 | n3)) & live & ~done) != 0u;
+                if (conflict) {
+                    if constexpr (TBL)
+                        slot = kPack ? (((xs & 0xFFFFu) == 0u) | ((xs >> 16) == 0u)) : ((xs == 0u) | (b == be));
                     const unsigned sm = group_ballot<S>(gmask, gbase, slot) & live & ~done;
                     if (sm) {
                         lim_eff = __ffs(sm) - 1;             // > e
@@ -316,16 +354,34 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
                         cor += (int)(nj[q] == ie) - (int)(ni[q] == ie) + (int)(ni[q] == je) -
                                (int)(nj[q] == je);
                     dk += 2 * cor;
-                    eval = true;
+                    wx = (kw + dk) >> ks;
+                    off = (unsigned)wx >= (unsigned)wn;
+                    ld = wl[off ? (kw >> ks) : wx];
+                    acc = (dk == 0) | off | (ld <= u + base);
                 }
+                v = ld - mF;
+                evb = group_ballot<S>(gmask, gbase, acc);
+                offb = group_ballot<S>(gmask, gbase, off);
                 if ((live & ~done) == 0u) {
                     c = lim_eff;
                     break;
                 }
             }
+            bc = k >> ks;
             cur = u + (int64_t)c * F;
             pend = c - ent;
             if (c == 0) stop = 4;                  // step t always fits the window
+            if constexpr (TBL) {
+                __syncwarp(gmask);
+                const uint32_t tm = (uint32_t)A.tbl_mask;
+#pragma unroll
+                for (int q = 0; q < zc; ++q) {
+                    tbl[ni[q] & tm] = 0u;
+                    tbl[nj[q] & tm] = 0u;
+                }
+                tbl[tm + 1 + (a & tm)] = 0u;
+                tbl[tm + 1 + ((ell + b) & tm)] = 0u;
+            }
             // apply the accepted exchanges (distinct slots, distinct sites)
             if ((accm >> m) & 1u) {
                 perm[a] = (IDX)j;
@@ -463,7 +519,7 @@ __device__ __forceinline__ void group_copy(uint32_t* dst, const uint32_t* src, i
 // Persistent walker: every group pops lines from the work queue until it is
 // empty.  With one group and a one-entry queue the same kernel is the plain
 // one-launch-per-line form.
-template <int LAT, int S, bool DET, typename IDX>
+template <int LAT, int S, bool DET, typename IDX, bool TBL>
 __global__ void walk_kernel(const WalkArgs A)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -476,6 +532,15 @@ __global__ void walk_kernel(const WalkArgs A)
     uint8_t* slot = smem + (size_t)gid * (size_t)A.slot_bytes;
     uint8_t* win = slot;
     slot += kWinBytes;
+    uint32_t* tbl = nullptr;
+    if constexpr (TBL) {
+        // the conflict filter table starts empty and is left empty by every batch
+        tbl = reinterpret_cast<uint32_t*>(slot);
+        const int words = 2 * (A.tbl_mask + 1);
+        for (int x = m; x < words; x += S) tbl[x] = 0u;
+        __syncwarp(gmask);
+        slot += (size_t)words * 4;
+    }
     // per-line strides are padded to 16 bytes: pstride list entries, W spin words
     const int pstride = A.pstride, W = A.g.W;
     const int perm_words = (int)((size_t)pstride * sizeof(IDX) / 4);
@@ -496,13 +561,13 @@ __global__ void walk_kernel(const WalkArgs A)
                           perm_words, m);
             group_copy<S>(ssp, gsp, W, m);
             __syncwarp(gmask);
-            walk_line<LAT, S, DET, IDX>(A, li, m, gbase, gmask, sperm, ssp, win);
+            walk_line<LAT, S, DET, IDX, TBL>(A, li, m, gbase, gmask, sperm, ssp, win, tbl);
             group_copy<S>(reinterpret_cast<uint32_t*>(gperm), reinterpret_cast<const uint32_t*>(sperm),
                           perm_words, m);
             group_copy<S>(gsp, ssp, W, m);
             __syncwarp(gmask);
         } else {
-            walk_line<LAT, S, DET, IDX>(A, li, m, gbase, gmask, gperm, gsp, win);
+            walk_line<LAT, S, DET, IDX, TBL>(A, li, m, gbase, gmask, gperm, gsp, win, tbl);
         }
     }
 }

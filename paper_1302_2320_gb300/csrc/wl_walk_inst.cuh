@@ -9,11 +9,11 @@
 
 namespace wl {
 
-template <int LAT, int S, bool DET, typename IDX>
+template <int LAT, int S, bool DET, typename IDX, bool TBL>
 cudaError_t walk_one(dim3 grid, dim3 block, size_t smem, cudaStream_t s, const WalkArgs& a,
                      int* bps)
 {
-    auto* fn = walk_kernel<LAT, S, DET, IDX>;
+    auto* fn = walk_kernel<LAT, S, DET, IDX, TBL>;
     // The dynamic shared-memory limit is a property of the kernel function,
     // shared by every handle: raise it to the device maximum (outside stream
     // capture) and never lower it, so a captured launch of one handle stays
@@ -38,16 +38,26 @@ cudaError_t walk_one(dim3 grid, dim3 block, size_t smem, cudaStream_t s, const W
     return cudaGetLastError();
 }
 
+// The conflict-filter form (a.tbl_mask != 0) exists for 32 lanes per walker.
 template <int LAT, int S>
 cudaError_t walk_s(bool det, bool idx16, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                    const WalkArgs& a, int* bps)
 {
-    if (det) {
-        if (idx16) return walk_one<LAT, S, true, uint16_t>(grid, block, smem, s, a, bps);
-        return walk_one<LAT, S, true, uint32_t>(grid, block, smem, s, a, bps);
+    if (S == 32 && a.tbl_mask != 0) {
+        if (det) {
+            if (idx16) return walk_one<LAT, S, true, uint16_t, true>(grid, block, smem, s, a, bps);
+            return walk_one<LAT, S, true, uint32_t, true>(grid, block, smem, s, a, bps);
+        }
+        if (idx16) return walk_one<LAT, S, false, uint16_t, true>(grid, block, smem, s, a, bps);
+        return walk_one<LAT, S, false, uint32_t, true>(grid, block, smem, s, a, bps);
     }
-    if (idx16) return walk_one<LAT, S, false, uint16_t>(grid, block, smem, s, a, bps);
-    return walk_one<LAT, S, false, uint32_t>(grid, block, smem, s, a, bps);
+    if (a.tbl_mask != 0) return cudaErrorInvalidValue;
+    if (det) {
+        if (idx16) return walk_one<LAT, S, true, uint16_t, false>(grid, block, smem, s, a, bps);
+        return walk_one<LAT, S, true, uint32_t, false>(grid, block, smem, s, a, bps);
+    }
+    if (idx16) return walk_one<LAT, S, false, uint16_t, false>(grid, block, smem, s, a, bps);
+    return walk_one<LAT, S, false, uint32_t, false>(grid, block, smem, s, a, bps);
 }
 
 template <int LAT>

@@ -2,10 +2,10 @@
 
     python tests/golden/make_golden.py [--threads N]
 
-square_L12_exact.txt: exact ln g_kl of the periodic 12x12 square Ising lattice
-(N = 144, N_B = 288) for l = 0..72, every k with g_kl > 0, from the oracle's
-site-by-site transfer matrix (the exact surface that Eq. 2 sums over; the
-paper cites transfer-matrix surfaces up to 12x12).  Columns: l, k, ln g_kl.
+square_L{8,12}_exact.txt: exact ln g_kl of the periodic 8x8 and 12x12 square
+Ising lattices (N_B = 2N) for l = 0..N/2, every k with g_kl > 0, from the
+oracle's site-by-site transfer matrix (the exact surface that Eq. 2 sums over;
+the paper cites transfer-matrix surfaces up to 12x12).  Columns: l, k, ln g_kl.
 cubic_L3_exact.txt: exact g_kl of the periodic 3x3x3 simple cubic lattice by
 enumeration of all 2^27 configurations.  Columns: l, k, g_kl.
 square_L{16,32,64}_gk_exact.txt: exact zero-field ln g_k of the periodic L x L
@@ -27,18 +27,19 @@ import numpy as np  # noqa: E402
 import oracle  # noqa: E402
 
 
-def write_square_l12(threads):
+def write_square_tm(L, threads):
     t0 = time.time()
-    g = oracle.tm_square(12, ell_max=72, nthreads=threads)
-    path = os.path.join(HERE, "square_L12_exact.txt")
+    N = L * L
+    g = oracle.tm_square(L, ell_max=N // 2, nthreads=threads)
+    path = os.path.join(HERE, f"square_L{L}_exact.txt")
     with open(path, "w") as f:
-        f.write("# exact ln g_kl, periodic 12x12 square lattice, transfer matrix "
+        f.write(f"# exact ln g_kl, periodic {L}x{L} square lattice, transfer matrix "
                 "(tests/golden/make_golden.py)\n# l k ln_g\n")
-        for ell in range(73):
-            for k in range(0, 289):
+        for ell in range(N // 2 + 1):
+            for k in range(0, 2 * N + 1):
                 if g[k, ell] > 0:
                     f.write(f"{ell} {k} {math.log(g[k, ell]):.17g}\n")
-    print(f"square L=12: {time.time() - t0:.1f} s -> {path}")
+    print(f"square L={L}: {time.time() - t0:.1f} s -> {path}")
 
 
 def write_cubic_l3():
@@ -72,12 +73,15 @@ def write_square_gk(L):
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--threads", type=int, default=os.cpu_count() or 1)
-    ap.add_argument("--only", choices=["square", "cubic", "gk"], default=None)
+    ap.add_argument("--only", choices=["square", "square8", "cubic", "gk"], default=None)
     a = ap.parse_args()
     if a.only in (None, "cubic"):
         write_cubic_l3()
+    if a.only == "square8":
+        write_square_tm(8, a.threads)
     if a.only in (None, "square"):
-        write_square_l12(a.threads)
+        write_square_tm(8, a.threads)
+        write_square_tm(12, a.threads)
     if a.only in (None, "gk"):
         for L in (16, 32, 64):
             write_square_gk(L)

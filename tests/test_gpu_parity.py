@@ -143,6 +143,16 @@ def test_other_lattices_bit_exact(lattice, L, budget):
         assert_line_equal(h, ell, ref[ell], lattice)
 
 
+@pytest.mark.parametrize("tail", [0, 1])
+def test_square_L12_tail_shape_bit_exact(l12_ref, tail):
+    """32 lanes per walker with fewer lines than SMs: the one-walker-per-SM
+    shape with the conflict filter table (tail = 1, the default) and the
+    ordinary shape (tail = 0) both give the oracle's chain."""
+    h = run_gpu("square", 12, 1, 1e-8, 1000, 10**7, mapping=32, tail=tail)
+    for ell in range(73):
+        assert_line_equal(h, ell, l12_ref[ell], f"tail={tail}")
+
+
 @pytest.mark.parametrize("lattice,L,mapping", [("square", 3, 32), ("square", 4, 32), ("square", 5, 16),
                                                ("triangular", 3, 32), ("triangular", 4, 8),
                                                ("cubic", 3, 32), ("square_open", 3, 32),

@@ -55,3 +55,28 @@ def test_request_larger_than_budget_is_refused():
         srv.submit("square", 64)
     assert e.value.status == 2                             # WL_ENOMEM
     srv.close()
+
+
+def test_pooled_handles_are_reused_and_evicted():
+    """Requests of one lattice reuse a finished request's handle (same results
+    as solo runs); with room for one handle at a time, alternating lattices
+    evict the idle handle of the other lattice and still complete."""
+    reqs = [("square", 10, 11), ("square", 10, 12), ("triangular", 6, 13), ("square", 10, 14),
+            ("triangular", 6, 15)]
+    budget = max(wl.wl_required_bytes(wl.LATTICES[lat], L) for lat, L, _ in reqs)
+    srv = wl.Server(hbm_budget=budget, max_active=2)
+    ids = [srv.submit(lat, L, seed=seed, ln_f_min=U, check_interval=C, move_budget=300_000)
+           for lat, L, seed in reqs]
+    for rid, (lat, L, seed) in zip(ids, reqs):
+        assert srv.wait(rid, 300.0) in (wl.WL_OK, wl.WL_ENOTCONVERGED)
+        h = wl.Handle(lat, L, seed=seed, check_interval=C, move_budget=300_000)
+        h.run(U, 0.8)
+        h.assemble()
+        ref, _ = h.get_surface()
+        h.close()
+        assert np.array_equal(srv.result(rid), ref), (lat, L, seed)
+    infos = [srv.info(rid) for rid in ids]
+    spans = sorted((i["start_s"], i["finish_s"]) for i in infos)
+    for a, b in zip(spans, spans[1:]):
+        assert b[0] >= a[1] - 1e-9           # one handle's room: never two at once
+    srv.close()

@@ -332,6 +332,28 @@ def test_golden_l12_closed_forms():
     assert math.isclose(g[72][NB], math.log(2), abs_tol=1e-12)
 
 
+def test_golden_l8_closed_forms_and_tm():
+    """The stored 8x8 surface: row sums C(N, l), the closed forms of the small
+    lines and of l = N/2 (bands 2L at k = 2L, Neel at k = N_B), and equality
+    with the oracle's TM recomputed here (0.4 s)."""
+    L, N, NB = 8, 64, 128
+    g = {}
+    for ell, k, lg in np.loadtxt(os.path.join(HERE, "golden", "square_L8_exact.txt")):
+        g.setdefault(int(ell), {})[int(k)] = float(lg)
+    assert sorted(g) == list(range(33))
+    for ell, row in g.items():
+        lse = np.logaddexp.reduce(np.array(list(row.values())))
+        assert math.isclose(lse, math.log(math.comb(N, ell)), rel_tol=0, abs_tol=1e-11), ell
+        assert max(row) == min(4 * ell, NB) and all(k % 2 == 0 for k in row)
+    assert math.isclose(g[2][6], math.log(NB), abs_tol=1e-12)
+    assert math.isclose(g[32][2 * L], math.log(2 * L), abs_tol=1e-12)
+    assert math.isclose(g[32][NB], math.log(2), abs_tol=1e-12)
+    tm = oracle.tm_square(L, ell_max=N // 2)
+    for ell, row in g.items():
+        for k, lg in row.items():
+            assert math.isclose(lg, math.log(tm[k, ell]), abs_tol=1e-12)
+
+
 def test_golden_l12_matches_tm_rows_at_small_l():
     """Low-l rows of the stored surface recomputed with a TM truncated at l=3."""
     g = load_l12_exact()
