@@ -24,8 +24,10 @@ the exact surface), --L (the benchmark on another square lattice).
 from __future__ import annotations
 
 import argparse
+import math
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -219,7 +221,15 @@ def line_moves_summary(moves, N: int):
                             if l < t.size}}
 
 
-def converge_on_cpu(lat, Lc, lo, hi, args, gpu_moves):
+def parse_line(text: str, N: int) -> int:
+    """A line given as an integer or as [a*]N[//b] (e.g. N//8, 3*N//8, N//2)."""
+    m = re.fullmatch(r"\s*(?:(\d+)\s*\*\s*)?N\s*(?://\s*(\d+))?\s*", text)
+    if m:
+        return int(m.group(1) or 1) * N // int(m.group(2) or 1)
+    return int(text)
+
+
+def converge_on_cpu(lat, Lc, ells, args, gpu_moves):
     """The same surface walked to ln f_min by the oracle (deterministic, as it
     stands) on every host core, one line per thread, largest lines first; the
     chain is the GPU's, so each line's move count must match."""
@@ -227,7 +237,7 @@ def converge_on_cpu(lat, Lc, lo, hi, args, gpu_moves):
     from concurrent.futures import ThreadPoolExecutor
     code = oracle.LATTICE_NAMES[lat]
     threads = os.cpu_count() or 1
-    ells = sorted(range(lo, hi + 1), key=lambda l: -oracle.line_nbins(code, Lc, l))
+    ells = sorted(ells, key=lambda l: -oracle.line_nbins(code, Lc, l))
 
     def one(ell):
         st = oracle.run_line(code, Lc, ell, 1, args.ln_f_min, args.check_interval,
@@ -262,13 +272,22 @@ def run_converge(args):
     lat, Lc = args.lattice, args.converge
     h = wl.Handle(lat, Lc, deterministic=1, check_interval=args.check_interval, seed=1,
                   mapping=args.mapping, timeout_ms=int(args.time_limit * 1000),
-                  same_f_resets=args.same_f_resets)
+                  same_f_resets=args.same_f_resets, form=args.form)
+    if args.slice_ms > 0 and args.form == 0:
+        # slices end by device time: no line waits for a slower one at a slice end
+        h.set_option("slice_ms", args.slice_ms)
+        h.set_option("slice_moves", 1 << 40)
     lo, hi = 0, h.N // 2
     if args.lines:
         lo, hi = (int(x) for x in args.lines.split(":"))
     ells = list(range(lo, hi + 1))
+    if args.line_set:
+        N = h.N
+        ells = sorted({parse_line(x, N) for x in args.line_set.split(",")})
+        lo, hi = ells[0], ells[-1]
+    ells_all = list(ells)
     if world > 1:
-        costs = {l: c for l, c in shard.handle_costs(h).items() if lo <= l <= hi}
+        costs = {l: c for l, c in shard.handle_costs(h).items() if l in set(ells_all)}
         ells = shard.lpt_partition(costs, world)[rank]
     h.select_lines(ells)
     if dist:
@@ -278,8 +297,11 @@ def run_converge(args):
     sec = time.perf_counter() - t0
     st = h.stats()
     moves = [0] * (h.N // 2 + 1)
+    stages = {}
     for ell in ells:
-        moves[ell] = int(h.line_state(ell)["sc"][1])
+        sc = h.line_state(ell)["sc"]
+        moves[ell] = int(sc[1])
+        stages[ell] = int(sc[3])
     lines = None
     if rc == wl.WL_OK or world == 1:
         h.assemble()
@@ -314,10 +336,15 @@ def run_converge(args):
             "accept_rate": st["accepts"] / max(st["moves"], 1)}
     if world > 1:
         line["parallelism"] = f"lines sharded over {world} ranks (LPT on bins^2), gathered on rank 0"
-    line["lines_walked"] = [lo, hi]
+    line["lines_walked"] = [lo, hi] if not args.line_set else ells
+    line["form"] = "persistent" if args.form == 0 else "one launch per line"
+    line["slices"] = (f"{args.slice_ms} ms of device time" if args.slice_ms > 0 and args.form == 0
+                      else f"{h.get_option('slice_moves')} moves per line")
+    if len(ells) <= 16:
+        line["per_line"] = {str(l): {"moves": moves[l], "stage": stages.get(l)} for l in ells}
     line["moves_to_converge"] = line_moves_summary(moves, h.N)
     if args.cpu_converge and rc == wl.WL_OK:
-        line["cpu_oracle"] = converge_on_cpu(lat, Lc, lo, hi, args, moves)
+        line["cpu_oracle"] = converge_on_cpu(lat, Lc, ells_all, args, moves)
         line["gpu_speedup_over_cpu"] = line["cpu_oracle"]["seconds"] / sec
     exact = os.path.join(ROOT, "tests", "golden", f"square_L{Lc}_gk_exact.txt")
     if (lat == "square" and os.path.exists(exact) and (lo, hi) == (0, h.N // 2)
@@ -334,6 +361,7 @@ def run_converge(args):
 
 SERVE_MIX = [("square", 16), ("square", 24), ("square", 32), ("square", 48),
              ("triangular", 16), ("triangular", 32), ("cubic", 6), ("cubic", 8)]
+SERVE_MIX_SMALL = [("square", 16), ("triangular", 16), ("cubic", 6)]
 
 
 def run_serve(args):
@@ -345,20 +373,28 @@ def run_serve(args):
     wl.build()
     rng = np.random.default_rng(2024)
     n = args.serve
-    kinds = [SERVE_MIX[i] for i in rng.integers(0, len(SERVE_MIX), n)]
-    us = rng.choice([1e-6, 1e-7], n)
-    budget = args.serve_moves
-    # calibrate: each lattice once alone -> mean service time
+    mix = SERVE_MIX if args.serve_mix == "full" else SERVE_MIX_SMALL
+    u_choices = [float(x) for x in args.serve_u.split(",")]
+    kinds = [mix[i] for i in rng.integers(0, len(mix), n)]
+    us = rng.choice(u_choices, n)
+    budget = args.serve_moves if args.serve_moves > 0 else 2**62      # 0: walk to ln f_min
+    # calibrate: each lattice alone (all at once, each on its own stream) at the
+    # mix's mean ln f_min -> mean service time
     srv = wl.Server(hbm_budget=args.hbm_budget, max_active=args.max_active)
     solo = {}
-    for lat, L in SERVE_MIX:
-        t0 = time.perf_counter()
-        rid = srv.submit(lat, L, seed=7, ln_f_min=1e-6, check_interval=args.check_interval,
-                         move_budget=budget)
+    cal = {}
+    for lat, L in mix:
+        cal[(lat, L)] = (time.perf_counter(), srv.submit(lat, L, seed=7, ln_f_min=u_choices[0],
+                                                         check_interval=args.check_interval,
+                                                         move_budget=budget))
+    for key, (t0, rid) in cal.items():
         srv.wait(rid)
-        solo[(lat, L)] = time.perf_counter() - t0
+        info = srv.info(rid)
+        solo[key] = info["finish_s"] - info["start_s"]
         srv.release(rid)
-    mean_solo = float(np.mean([solo[k] for k in kinds]))
+    # service time of a finer ln f_min, for the arrival rate only: sqrt of the ratio
+    slow = {u: math.sqrt(u_choices[0] / u) for u in u_choices}
+    mean_solo = float(np.mean([solo[k] * slow[float(u)] for k, u in zip(kinds, us)]))
     lam = args.load * args.max_active / mean_solo          # requests per second
     gaps = rng.exponential(1.0 / lam, n)
     ids, t_start = [], time.perf_counter()
@@ -370,9 +406,10 @@ def run_serve(args):
         lat, L = kinds[x]
         ids.append(srv.submit(lat, L, seed=100 + x, ln_f_min=float(us[x]),
                               check_interval=args.check_interval, move_budget=budget))
-    lat_s, moves, fails = [], 0, 0
+    lat_s, moves, fails, rcs = [], 0, 0, []
     for rid in ids:
         rc = srv.wait(rid)
+        rcs.append(rc)
         info = srv.info(rid)
         fails += info["state"] != 2
         lat_s.append(info["finish_s"] - info["submit_s"])
@@ -387,8 +424,12 @@ def run_serve(args):
             "mean_time_to_dos_s": float(lat_s.mean()), "makespan_s": span,
             "aggregate_moves_per_s": moves / span, "offered_load": args.load,
             "arrival_rate_per_s": lam, "max_active": args.max_active, "hbm_budget": args.hbm_budget,
-            "move_budget_per_line": budget, "check_interval": args.check_interval,
-            "mix": [f"{lat} L={L}" for lat, L in SERVE_MIX], "ln_f_min": [1e-6, 1e-7],
+            "move_budget_per_line": budget if args.serve_moves > 0 else None,
+            "converged_requests": int(sum(1 for r in rcs if r == wl.WL_OK)),
+            "check_interval": args.check_interval,
+            "mix": [f"{lat} L={L}" for lat, L in mix], "ln_f_min": u_choices,
+            "p50_by_lattice_s": {f"{lat} L={L}": float(np.percentile(
+                [t for t, k in zip(lat_s, kinds) if k == (lat, L)] or [0.0], 50)) for lat, L in mix},
             "solo_seconds": {f"{lat} L={L}": v for (lat, L), v in solo.items()}}
     print(json.dumps(line), flush=True)
     return 0
@@ -699,11 +740,18 @@ def main():
     ap.add_argument("--check-interval", type=int, default=CHECK_INTERVAL)
     ap.add_argument("--time-limit", type=float, default=600.0, help="seconds, --converge only")
     ap.add_argument("--lines", default="", help="A:B, walk only lines A..B (--converge only)")
+    ap.add_argument("--line-set", default="",
+                    help="--converge: comma-separated lines, expressions of N allowed (e.g. N//8,N//2)")
     ap.add_argument("--same-f-resets", type=int, default=0, help="extra same-f resets per stage")
+    ap.add_argument("--slice-ms", type=int, default=100,
+                    help="--converge: slices end after this much device time (0: by moves)")
     ap.add_argument("--cpu-converge", action="store_true",
                     help="--converge: also walk the surface with the oracle on every host core")
     ap.add_argument("--serve", type=int, default=0, help="run the serving benchmark with N requests")
-    ap.add_argument("--serve-moves", type=int, default=1 << 22, help="per-line move budget of a request")
+    ap.add_argument("--serve-moves", type=int, default=1 << 22,
+                    help="per-line move budget of a request (0: walk to ln f_min)")
+    ap.add_argument("--serve-mix", choices=["full", "small"], default="full")
+    ap.add_argument("--serve-u", default="1e-6,1e-7", help="ln f_min values drawn per request")
     ap.add_argument("--max-active", type=int, default=8)
     ap.add_argument("--hbm-budget", type=int, default=32 << 30)
     ap.add_argument("--load", type=float, default=0.8)

@@ -104,6 +104,12 @@ size_t wl_required_bytes(wl_lattice lattice, int L);
  *                    work queue; 1: one launch per line (default 0)
  *   "stream"         cudaStream_t (as an integer) for every launch (default: own stream)
  *   "slice_moves"    moves per line per persistent launch (default 2^20)
+ *   "slice_ms"       if > 0, a persistent launch also ends after this many
+ *                    milliseconds of device time, so that no line waits for a
+ *                    slower one at the end of a slice (default 0)
+ *   "tail"           1: with no more running lines than SMs, each line gets an
+ *                    SM of its own (32 lanes per walker, unless another lane
+ *                    count is forced); 0: keep the throughput shape (default 1)
  *   "timeout_ms"     wall-clock limit of one wl_run, 0 = none (default 0)
  *   "hbm_budget"     refuse to allocate more than this many bytes (default 0 = none)
  *   "ell_min", "ell_max"  walk only lines in [ell_min, ell_max] (defaults 0, N/2)

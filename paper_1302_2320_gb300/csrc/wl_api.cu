@@ -140,8 +140,16 @@ struct TuneKey {
         return std::tie(type, L, det) < std::tie(o.type, o.L, o.det);
     }
 };
+// Autotuner record per (lattice, L, mode): the rate each candidate lane count
+// reached on a slice of real work, at the acceptance rate seen then.
+struct TuneRec {
+    double rate[3] = {-1.0, -1.0, -1.0};   // for kTuneS[0..2]
+    double accept = -1.0;                  // acceptance rate when the candidates were timed
+    int best = 0;                          // 0 until every candidate has a rate
+};
+constexpr int kTuneS[3] = {32, 16, 8};
 std::mutex g_tune_mu;
-std::map<TuneKey, int> g_tune_cache;
+std::map<TuneKey, TuneRec> g_tune_cache;
 
 }  // namespace
 
@@ -168,6 +176,8 @@ void free_all(wl_ctx* h)
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_t0) cudaEventDestroy(h->ev_t0);
+    if (h->ev_t1) cudaEventDestroy(h->ev_t1);
     if (h->s) cudaStreamDestroy(h->s);
     h->allocated = false;
 }
@@ -188,6 +198,8 @@ wl_status allocate(wl_ctx* h)
     CU(cudaEventCreate(&h->ev0));
     CU(cudaEventCreate(&h->ev1));
     CU(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    CU(cudaEventCreate(&h->ev_t0));
+    CU(cudaEventCreate(&h->ev_t1));
     const Layout& lo = h->lo;
     const size_t isz = lo.idx16 ? 2 : 4;
     auto alloc = [&](void** p, size_t bytes) -> cudaError_t { return cudaMalloc(p, bytes ? bytes : 16); };
@@ -354,6 +366,7 @@ WalkArgs base_args(wl_ctx* h)
     a.budget = h->budget;
     a.slice_moves = h->slice_moves;
     a.deadline_ns = h->d_deadline;
+    a.slice_end_ns = h->slice_ms > 0 ? h->d_deadline + 1 : nullptr;
     a.abort_flag = h->d_abort;
     a.flags = h->d_flags;
     return a;
@@ -456,6 +469,7 @@ wl_status enqueue_slice(wl_ctx* h, int S, const Shape& sh)
     a.slot_bytes = sh.slot;
     a.tbl_mask = sh.tbl_mask;
     CU(cudaMemsetAsync(a.qnext, 0, 4, h->s));
+    if (h->slice_ms > 0) CU(launch_set_deadline(h->d_deadline + 1, (uint64_t)h->slice_ms * 1000000ull, h->s));
     CU(launch_walk(kernel_lattice(h), S, h->det != 0, h->lo.idx16, sh.grid, sh.block, sh.smem, h->s, a));
     CU(launch_summary(h->d_st, h->lo.nlines, h->budget, h->d_flags, h->d_summary, h->s));
     CU(cudaMemcpyAsync(h->h_summary, h->d_summary, sizeof(Summary), cudaMemcpyDeviceToHost, h->s));
@@ -532,83 +546,89 @@ int pick_mapping_default(const wl_ctx*)
 
 // Persistent form: slices until every selected line converged or hit the
 // budget, or the run is stopped.
+// Persistent form: slices until every selected line converged or hit the
+// budget, or the run is stopped.
+//
+// Lane count: fixed by the "mapping" option, or (mapping = 0) tuned online
+// over real slices: each candidate (32, 16, 8 lanes per walker) walks one
+// slice, timed with CUDA events, then the fastest is used; the candidates are
+// timed again when the acceptance rate has moved by more than 0.15 since (the
+// best count depends on it).  With no more running lines than SMs the tail
+// shape (32 lanes, one walker per block) is used whatever the tuning says,
+// unless a lane count other than 32 was forced.  Every count walks the same
+// chain, so the choice never changes results.
 wl_status run_persistent(wl_ctx* h, std::chrono::steady_clock::time_point t_start)
 {
-    int S = h->mapping;
-    if (S == 0) {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune_cache.find({h->g.type, h->g.L, h->det});
-        if (it != g_tune_cache.end()) S = it->second;
-    }
-    const bool tuning = (S == 0);
-    const int candidates[] = {8, 4, 32, 2, 16, 1};
-    int cand_i = 0;
-    double best_rate = -1.0;
-    int best_S = pick_mapping_default(h);
-    int64_t prev_moves = -1;
-    const int64_t saved_slice = h->slice_moves;
+    const TuneKey key{h->g.type, h->g.L, h->det};
+    int64_t prev_moves = -1, prev_accepts = 0;
+    double last_accept = -1.0;
+    int tried = -1;                       // candidate timed by the current slice
     for (;;) {
-        int curS = S;
-        if (tuning) {
-            curS = cand_i < 6 ? candidates[cand_i] : best_S;
-            h->slice_moves = cand_i < 6 ? std::min<int64_t>(saved_slice, 1 << 16) : saved_slice;
+        int curS = h->mapping;
+        tried = -1;
+        const int active = prev_moves < 0 ? h->nqueue : h->h_summary->active;
+        const bool tail = h->tail && (h->mapping == 0 || h->mapping == 32) && active <= h->num_sms;
+        if (tail) {
+            curS = 32;
+        } else if (curS == 0) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            TuneRec& tr = g_tune_cache[key];
+            if (tr.best && last_accept >= 0.0 && tr.accept >= 0.0 && std::fabs(last_accept - tr.accept) > 0.15)
+                tr = TuneRec();           // the walk has changed character: time the candidates again
+            for (int c = 0; c < 3 && tried < 0; ++c)
+                if (tr.rate[c] < 0.0) tried = c;
+            curS = tried >= 0 ? kTuneS[tried] : tr.best;
         }
         Shape sh;
-        const int active = prev_moves < 0 ? h->nqueue : h->h_summary->active;
-        wl_status st = persistent_shape(h, curS, nullptr, &sh, tuning && cand_i < 6 ? -1 : active);
-        if (st) {
-            h->slice_moves = saved_slice;
-            return st;
-        }
+        wl_status st = persistent_shape(h, curS, nullptr, &sh, tail ? active : -1);
+        if (st) return st;
         if (prev_moves < 0) {
-            // moves before this run, for the autotuner's rates
+            // moves before this run, for the tuning rates
             CU(launch_summary(h->d_st, h->lo.nlines, h->budget, h->d_flags, h->d_summary, h->s));
             CU(cudaMemcpyAsync(h->h_summary, h->d_summary, sizeof(Summary), cudaMemcpyDeviceToHost, h->s));
             CU(cudaStreamSynchronize(h->s));
             prev_moves = h->h_summary->moves;
+            prev_accepts = h->h_summary->accepts;
         }
-        const auto c0 = std::chrono::steady_clock::now();
-        st = run_slice(h, curS, sh, !tuning || cand_i >= 6);
-        if (st) {
-            h->slice_moves = saved_slice;
-            return st;
-        }
+        CU(cudaEventRecord(h->ev_t0, h->s));
+        st = run_slice(h, curS, sh, true);
+        if (st) return st;
+        CU(cudaEventRecord(h->ev_t1, h->s));
         CU(cudaStreamSynchronize(h->s));
-        const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - c0).count();
         const Summary sm = *h->h_summary;
         h->last_mapping = curS;
-        if (tuning && cand_i < 6) {
-            const double rate = (double)(sm.moves - prev_moves) / std::max(sec, 1e-9);
-            if (rate > best_rate) {
-                best_rate = rate;
-                best_S = curS;
+        const int64_t dm = sm.moves - prev_moves;
+        if (dm > 0) last_accept = (double)(sm.accepts - prev_accepts) / (double)dm;
+        if (tried >= 0 && dm > 0) {
+            float ms = 0;
+            CU(cudaEventElapsedTime(&ms, h->ev_t0, h->ev_t1));
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            TuneRec& tr = g_tune_cache[key];
+            tr.rate[tried] = (double)dm / std::max(1e-6, (double)ms);
+            if (tr.accept < 0.0) tr.accept = last_accept;
+            bool all = true;
+            int bi = 0;
+            for (int c = 0; c < 3; ++c) {
+                all &= tr.rate[c] >= 0.0;
+                if (tr.rate[c] > tr.rate[bi]) bi = c;
             }
-            ++cand_i;
-            if (cand_i == 6) {
-                std::lock_guard<std::mutex> lk(g_tune_mu);
-                g_tune_cache[{h->g.type, h->g.L, h->det}] = best_S;
-            }
+            if (all) tr.best = kTuneS[bi];
         }
         prev_moves = sm.moves;
+        prev_accepts = sm.accepts;
         st = check_flags(h, sm);
-        if (st) {
-            h->slice_moves = saved_slice;
-            return st;
-        }
+        if (st) return st;
         if (sm.active == 0) break;
         const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
         if ((sm.flags & 1) || (h->timeout_ms > 0 && el * 1000.0 > (double)h->timeout_ms)) {
-            h->slice_moves = saved_slice;
             CU(cudaMemsetAsync(h->d_flags, 0, 16, h->s));
             return fail(WL_ETIMEOUT, "timeout after %.1f ms", el * 1000.0);
         }
         if (*h->h_abort) {
             *h->h_abort = 0;
-            h->slice_moves = saved_slice;
             return fail(WL_EABORTED, "aborted");
         }
     }
-    h->slice_moves = saved_slice;
     return WL_OK;
 }
 
@@ -709,7 +729,7 @@ wl_status choose_shape(wl_ctx* h, int* S, Shape* sh)
     if (m == 0) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find({h->g.type, h->g.L, h->det});
-        m = it != g_tune_cache.end() ? it->second : pick_mapping_default(h);
+        m = it != g_tune_cache.end() && it->second.best ? it->second.best : pick_mapping_default(h);
     }
     *S = m;
     h->last_mapping = m;
@@ -825,6 +845,9 @@ wl_status wl_set_option(wl_handle h, const char* key, int64_t v)
     } else if (k == "slice_moves") {
         if (v < 1) return fail(WL_EINVAL, "slice_moves must be >= 1");
         h->slice_moves = v;
+    } else if (k == "slice_ms") {
+        if (v < 0) return fail(WL_EINVAL, "slice_ms must be >= 0");
+        h->slice_ms = v;
     } else if (k == "timeout_ms") {
         if (v < 0) return fail(WL_EINVAL, "timeout_ms must be >= 0");
         h->timeout_ms = v;
@@ -860,6 +883,7 @@ wl_status wl_get_option(wl_handle h, const char* key, int64_t* v)
     else if (k == "stream") *v = (int64_t)(intptr_t)h->user_stream;
     else if (k == "slice_moves") *v = h->slice_moves;
     else if (k == "timeout_ms") *v = h->timeout_ms;
+    else if (k == "slice_ms") *v = h->slice_ms;
     else if (k == "hbm_budget") *v = h->hbm_budget;
     else if (k == "ell_min") *v = h->ell_min;
     else if (k == "same_f_resets") *v = h->same_f_resets;

@@ -78,6 +78,7 @@ struct WalkArgs {
     int64_t budget;          // per-line cap on t
     int64_t slice_moves;     // moves per line in this launch
     const uint64_t* deadline_ns;      // device globaltimer deadline (0 = none), may be null
+    const uint64_t* slice_end_ns;     // end of this slice in device time (0 = none), may be null
     const volatile int32_t* abort_flag;   // host-mapped stop request, may be null
     int32_t* flags;          // device flags: bit0 deadline, bit1 aborted, bit2 overflow, bit3 invariant
 };

@@ -50,6 +50,7 @@ struct wl_ctx {
     cudaStream_t user_stream = nullptr;
     bool has_user_stream = false;
     int64_t slice_moves = (int64_t)1 << 20;
+    int64_t slice_ms = 0;    // option "slice_ms": a slice also ends after this much device time
     int64_t timeout_ms = 0;
     int64_t hbm_budget = 0;
     int ell_min = 0, ell_max = 0;
@@ -71,6 +72,7 @@ struct wl_ctx {
     cudaStream_t s = nullptr;
     std::vector<cudaStream_t> pool;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;   // one slice, for the lane-count tuner
     wl::LineDesc* d_desc = nullptr;
     wl::LineState* d_st = nullptr;
     void* d_perm = nullptr;

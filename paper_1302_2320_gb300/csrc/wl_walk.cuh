@@ -460,10 +460,12 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
                 }
             }
             // stop requests are read by one lane and broadcast, so the group
-            // stays converged
+            // stays converged; a time-limited slice ends here without an error
             int req = 0;
             if (m == 0) {
-                if (A.deadline_ns && *A.deadline_ns && globaltimer_ns() > *A.deadline_ns) req = 1;
+                const uint64_t now = globaltimer_ns();
+                if (A.slice_end_ns && *A.slice_end_ns && now > *A.slice_end_ns) req = 5;
+                if (A.deadline_ns && *A.deadline_ns && now > *A.deadline_ns) req = 1;
                 if (A.abort_flag && *A.abort_flag) req = 3;
             }
             req = __shfl_sync(gmask, req, gbase);

@@ -374,56 +374,43 @@ def test_same_f_resets_bit_exact():
         assert_line_equal(h, ell, ref, "same-f resets")
 
 
-def _load_l12_exact():
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "square_L12_exact.txt")
-    data = np.loadtxt(path, comments="#")
-    out = {}
-    for ell, k, lg in data:
-        out.setdefault(int(ell), {})[int(k)] = float(lg)
-    return out
-
-
-def test_production_accuracy_square_L12_against_transfer_matrix():
-    """12x12, 73 lines, production mode, ln f_min = 1e-7, flatness checked every
-    10^7 moves, 4 seeds walked concurrently (one handle and stream each), against
-    the exact transfer-matrix surface.  With the 80%/80% test each stage ends at
-    its first check, so the accuracy is set by the moves per stage.  Measured at
-    this stage length: on lines with up to 73 bins (l <= 36) the normalised
-    ln g_kl away from the two ends of each line's spectrum is within a mean of
-    0.02 (the paper notes the largest deviations at the ends) with single bins up
-    to ~0.3 off; the larger lines reach a mean of ~0.03.  The bounds below hold
-    those figures with margin; a maximum of 0.1 on every bin needs stages about
-    ten times longer.  The measurement at ln f_min = 1e-8 over 8 seeds is
-    `bench.py --accuracy`."""
-    exact = _load_l12_exact()
+def test_production_accuracy_square_L6_at_the_stated_tolerance():
+    """The production tolerance (normalised ln g_kl within mean 0.02 and max 0.1
+    of the exact values at ln f_min = 1e-8) on the 6x6 periodic lattice, all 19
+    lines, 8 seeds walked concurrently (one handle and stream each), against
+    the oracle's transfer matrix.  With the 80%/80% test each stage ends at its
+    first check, so the accuracy is set by the moves per stage: flatness is
+    checked every 10^7 moves (the oracle reaches mean 0.004 / max 0.04 on the
+    inner bins at this stage length).  The lowest and highest k of each line,
+    where the paper also sees the largest deviations (its Fig. 5 discussion),
+    are held to mean 0.05 / max 0.3 separately.  The 12x12 surface at the same
+    tolerance is `bench.py --accuracy`."""
+    L, N = 6, 36
+    g = oracle.tm_square(L, ell_max=N // 2)
 
     def one(seed):
-        h = run_gpu("square", 12, seed, 1e-7, 10**7, 2**62, det=0)
-        assert h.stats()["lines_converged"] == 73
+        h = run_gpu("square", L, seed, 1e-8, 10**7, 2**62, det=0)
+        assert h.stats()["lines_converged"] == N // 2 + 1
         h.assemble()
-        return [h.get_lng(ell) for ell in range(73)]
+        out = [h.get_lng(ell) for ell in range(N // 2 + 1)]
+        h.close()
+        return out
 
-    with ThreadPoolExecutor(4) as ex:
-        surfaces = list(ex.map(one, range(1, 5)))
-    small, large, ends = [], [], []
+    with ThreadPoolExecutor(8) as ex:
+        surfaces = list(ex.map(one, range(1, 9)))
+    inner, ends = [], []
     for lines in surfaces:
-        for ell in range(73):
-            got = lines[ell]
-            ks = sorted(exact[ell])
-            assert set(np.nonzero(np.isfinite(got))[0]) == {k // 2 for k in ks}, ell
+        for ell in range(N // 2 + 1):
+            ks = [k for k in range(0, 2 * N + 1) if g[k, ell] > 0]
+            assert set(np.nonzero(np.isfinite(lines[ell]))[0]) == {k // 2 for k in ks}, ell
             for k in ks:
-                d = abs(got[k // 2] - exact[ell][k])
-                if k in (ks[0], ks[-1]) and len(ks) > 2:
-                    ends.append(d)
-                else:
-                    (small if ell <= 36 else large).append(d)
-    small, large, ends = np.array(small), np.array(large), np.array(ends)
-    print(f"L=12 production: l<=36 mean {small.mean():.4f} max {small.max():.4f}; "
-          f"l>36 mean {large.mean():.4f} max {large.max():.4f}; "
+                d = abs(lines[ell][k // 2] - math.log(g[k, ell]))
+                (ends if k in (ks[0], ks[-1]) and len(ks) > 2 else inner).append(d)
+    inner, ends = np.array(inner), np.array(ends)
+    print(f"L=6 production 1e-8: inner mean {inner.mean():.4f} max {inner.max():.4f}; "
           f"ends mean {ends.mean():.4f} max {ends.max():.4f}")
-    assert small.mean() <= 0.02 and small.max() <= 0.6
-    assert large.mean() <= 0.05 and large.max() <= 1.5
-    assert ends.mean() <= 0.5
+    assert inner.mean() <= 0.02 and inner.max() <= 0.1
+    assert ends.mean() <= 0.05 and ends.max() <= 0.3
 
 
 def test_square_L256_sampled_lines():
@@ -464,3 +451,12 @@ def test_line_shards_gather_to_the_full_surface():
     assert np.array_equal(offs, ref_offs)
     assert np.array_equal(vals, ref_vals)
     full.close()
+
+
+def test_time_limited_slices_bit_exact(l12_ref):
+    """Slices that end by device time (option slice_ms) instead of a move count
+    cut the walk at other places, and the chain is still the oracle's."""
+    h = run_gpu("square", 12, 1, 1e-8, 1000, 10**7, mapping=32, slice_ms=3, slice_moves=1 << 40)
+    assert h.stats()["launches"] > 4                     # several slices
+    for ell in range(73):
+        assert_line_equal(h, ell, l12_ref[ell], "slice_ms=3")
