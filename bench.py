@@ -229,10 +229,12 @@ def parse_line(text: str, N: int) -> int:
     return int(text)
 
 
-def converge_on_cpu(lat, Lc, ells, args, gpu_moves):
+def converge_on_cpu(lat, Lc, ells, args, gpu_moves, to_gpu_moves=False):
     """The same surface walked to ln f_min by the oracle (deterministic, as it
     stands) on every host core, one line per thread, largest lines first; the
-    chain is the GPU's, so each line's move count must match."""
+    chain is the GPU's, so each line's move count must match.  With
+    to_gpu_moves each line is walked only as far as the GPU got (a run that hit
+    its time limit): the time the host cores need for the same progress."""
     import oracle
     from concurrent.futures import ThreadPoolExecutor
     code = oracle.LATTICE_NAMES[lat]
@@ -241,16 +243,25 @@ def converge_on_cpu(lat, Lc, ells, args, gpu_moves):
 
     def one(ell):
         st = oracle.run_line(code, Lc, ell, 1, args.ln_f_min, args.check_interval,
-                             int(FLATNESS * 1000), 2**62, 0, same_f_resets=args.same_f_resets)
+                             int(FLATNESS * 1000), gpu_moves[ell] if to_gpu_moves else 2**62, 0,
+                             same_f_resets=args.same_f_resets)
+        return ell, st.t
+
+    def one_c(ell):
+        Cl = max(args.check_interval, args.check_per_bin * oracle.line_nbins(code, Lc, ell))
+        st = oracle.run_line(code, Lc, ell, 1, args.ln_f_min, Cl,
+                             int(FLATNESS * 1000), gpu_moves[ell] if to_gpu_moves else 2**62, 0,
+                             same_f_resets=args.same_f_resets)
         return ell, st.t
     t0 = time.perf_counter()
     with ThreadPoolExecutor(threads) as ex:
-        res = dict(ex.map(one, ells))
+        res = dict(ex.map(one_c if args.check_per_bin else one, ells))
     sec = time.perf_counter() - t0
     same = all(res[l] == gpu_moves[l] for l in ells)
     return {"seconds": sec, "cores": threads, "kind": "oracle", "moves": int(sum(res.values())),
             "same_moves_per_line_as_gpu": bool(same),
-            "sample": "the whole surface, every line to ln f_min, one thread per line"}
+            "sample": ("every walked line to the GPU's move count (same chain), one thread per line"
+                       if to_gpu_moves else "every walked line to ln f_min, one thread per line")}
 
 
 def run_converge(args):
@@ -273,6 +284,8 @@ def run_converge(args):
     h = wl.Handle(lat, Lc, deterministic=1, check_interval=args.check_interval, seed=1,
                   mapping=args.mapping, timeout_ms=int(args.time_limit * 1000),
                   same_f_resets=args.same_f_resets, form=args.form)
+    if args.check_per_bin:
+        h.set_option("check_per_bin", args.check_per_bin)
     if args.slice_ms > 0 and args.form == 0:
         # slices end by device time: no line waits for a slower one at a slice end
         h.set_option("slice_ms", args.slice_ms)
@@ -328,6 +341,7 @@ def run_converge(args):
             return 0
     line = {"mode": "time_to_ln_f_min", "lattice": lat, "L": Lc, "N": h.N, "lines": st["lines"],
             "ln_f_min": args.ln_f_min, "check_interval": args.check_interval,
+            "check_per_bin": args.check_per_bin,
             "same_f_resets": args.same_f_resets, "n_gpus": world,
             "status": "converged" if rc == wl.WL_OK else "time limit",
             "seconds": sec, "lines_converged": st["lines_converged"],
@@ -343,8 +357,8 @@ def run_converge(args):
     if len(ells) <= 16:
         line["per_line"] = {str(l): {"moves": moves[l], "stage": stages.get(l)} for l in ells}
     line["moves_to_converge"] = line_moves_summary(moves, h.N)
-    if args.cpu_converge and rc == wl.WL_OK:
-        line["cpu_oracle"] = converge_on_cpu(lat, Lc, ells_all, args, moves)
+    if args.cpu_converge and (rc == wl.WL_OK or len(ells_all) <= (os.cpu_count() or 1)):
+        line["cpu_oracle"] = converge_on_cpu(lat, Lc, ells_all, args, moves, to_gpu_moves=rc != wl.WL_OK)
         line["gpu_speedup_over_cpu"] = line["cpu_oracle"]["seconds"] / sec
     exact = os.path.join(ROOT, "tests", "golden", f"square_L{Lc}_gk_exact.txt")
     if (lat == "square" and os.path.exists(exact) and (lo, hi) == (0, h.N // 2)
@@ -745,6 +759,8 @@ def main():
     ap.add_argument("--same-f-resets", type=int, default=0, help="extra same-f resets per stage")
     ap.add_argument("--slice-ms", type=int, default=100,
                     help="--converge: slices end after this much device time (0: by moves)")
+    ap.add_argument("--check-per-bin", type=int, default=0,
+                    help="--converge: a line of n bins checks flatness every max(C, c n) moves")
     ap.add_argument("--cpu-converge", action="store_true",
                     help="--converge: also walk the surface with the oracle on every host core")
     ap.add_argument("--serve", type=int, default=0, help="run the serving benchmark with N requests")

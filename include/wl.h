@@ -98,6 +98,9 @@ size_t wl_required_bytes(wl_lattice lattice, int L);
  *                    chain bit-identical to the same walk taken one move at a
  *                    time (the CPU oracle's); 0: FP32 exp (default 1)
  *   "check_interval" C: flatness is tested whenever t is a multiple of C (default 1000)
+ *   "check_per_bin"  c > 0: a line with n bins tests flatness every max(C, c*n)
+ *                    moves instead, so lines with more bins get longer stages
+ *                    and find their rarest states before ln f shrinks (default 0)
  *   "move_budget"    per-line cap on the move counter t (default 2^62)
  *   "mapping"        lanes per walker S in {1,2,4,8,16,32}; 0 = autotune (default 0)
  *   "form"           0: one persistent launch over all lines with a device
@@ -118,7 +121,7 @@ size_t wl_required_bytes(wl_lattice lattice, int L);
  *                    while ln f is kept -- the extra reset the paper remarks
  *                    after Eq. 4 speeds the walk; its trigger is not given
  *                    there, this is one choice (default 0: off)
- * Setting "seed", "deterministic", "check_interval", "same_f_resets" or the
+ * Setting "seed", "deterministic", "check_interval", "check_per_bin", "same_f_resets" or the
  * line range after a run requires wl_reset().  Errors: WL_EINVAL (unknown key or bad value), WL_ESTATE. */
 wl_status wl_set_option(wl_handle h, const char* key, int64_t value);
 wl_status wl_get_option(wl_handle h, const char* key, int64_t* value);

@@ -363,6 +363,7 @@ WalkArgs base_args(wl_ctx* h)
     a.pstride = h->lo.pstride;
     a.same_f_resets = h->same_f_resets;
     a.C = h->C;
+    a.C_per_bin = h->C_per_bin;
     a.budget = h->budget;
     a.slice_moves = h->slice_moves;
     a.deadline_ns = h->d_deadline;
@@ -383,12 +384,12 @@ bool tail_shape(wl_ctx* h, int S, int active, Shape* sh)
     const size_t stg = (size_t)h->lo.pstride * isz + (size_t)h->lo.W * 4;
     const size_t cap = std::min<size_t>(h->max_smem, 220 * 1024);
     int H = 32;
-    while (H < h->g.N && H < 16384) H <<= 1;
-    size_t tbl = (size_t)2 * H * 4;
+    while (H < h->g.N && H < 32768) H <<= 1;
+    size_t tbl = (size_t)H * 4;
     int stage = (kWinBytes + tbl + stg <= cap && stg <= 64 * 1024) ? 1 : 0;
     while (kWinBytes + tbl + (stage ? stg : 0) > cap && H > 32) {
         H >>= 1;
-        tbl = (size_t)2 * H * 4;
+        tbl = (size_t)H * 4;
     }
     const size_t slot = kWinBytes + tbl + (stage ? stg : 0);
     if (slot > cap) return false;
@@ -817,7 +818,7 @@ wl_status wl_set_option(wl_handle h, const char* key, int64_t v)
 {
     if (!valid_handle(h) || !key) return fail(WL_EINVAL, "NULL handle or key");
     const std::string k(key);
-    const bool semantic = (k == "seed" || k == "deterministic" || k == "check_interval" ||
+    const bool semantic = (k == "seed" || k == "deterministic" || k == "check_interval" || k == "check_per_bin" ||
                            k == "ell_min" || k == "ell_max" || k == "same_f_resets");
     if (semantic && h->initialized)
         return fail(WL_ESTATE, "option '%s' changes the walk; call wl_reset first", key);
@@ -829,6 +830,9 @@ wl_status wl_set_option(wl_handle h, const char* key, int64_t v)
     } else if (k == "check_interval") {
         if (v < 1 || v > 0x7FFFFFFFll) return fail(WL_EINVAL, "check_interval must be in [1, 2^31-1]");
         h->C = v;
+    } else if (k == "check_per_bin") {
+        if (v < 0 || v > (1ll << 24)) return fail(WL_EINVAL, "check_per_bin must be in [0, 2^24]");
+        h->C_per_bin = v;
     } else if (k == "move_budget") {
         if (v < 0) return fail(WL_EINVAL, "move_budget must be >= 0");
         h->budget = v;
@@ -877,6 +881,7 @@ wl_status wl_get_option(wl_handle h, const char* key, int64_t* v)
     if (k == "seed") *v = h->seed;
     else if (k == "deterministic") *v = h->det;
     else if (k == "check_interval") *v = h->C;
+    else if (k == "check_per_bin") *v = h->C_per_bin;
     else if (k == "move_budget") *v = h->budget;
     else if (k == "mapping") *v = h->mapping;
     else if (k == "form") *v = h->form;

@@ -73,8 +73,9 @@ struct WalkArgs {
     int32_t slot_bytes;      // shared bytes per walker slot (window + staged list/spins)
     int32_t pstride;         // list entries per line, N rounded up to 16 bytes
     int32_t same_f_resets;   // R > 0: extra histogram resets at unchanged f (see walk_line)
-    int32_t tbl_mask;        // conflict filter table: 2 x (tbl_mask + 1) words per walker (tail kernel)
+    int32_t tbl_mask;        // conflict filter table: tbl_mask + 1 words per walker (tail kernel)
     int64_t C;               // flatness check interval
+    int64_t C_per_bin;       // > 0: a line of n bins checks every max(C, C_per_bin * n) moves
     int64_t budget;          // per-line cap on t
     int64_t slice_moves;     // moves per line in this launch
     const uint64_t* deadline_ns;      // device globaltimer deadline (0 = none), may be null

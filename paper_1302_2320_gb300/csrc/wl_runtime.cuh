@@ -44,6 +44,7 @@ struct wl_ctx {
     uint32_t seed = 1;
     int det = 1;
     int64_t C = 1000;
+    int64_t C_per_bin = 0;   // option "check_per_bin"
     int64_t budget = (int64_t)1 << 62;
     int mapping = 0;
     int form = 0;

@@ -126,9 +126,11 @@ wl_status start_request(Request* r)
         }
     }
     if ((st = wl_reset(p->h))) return st;
+    // slices end by device time (50 ms), so a request's lines never wait for
+    // its slowest line at a slice end
     const std::pair<const char*, int64_t> opts[] = {
         {"seed", r->seed}, {"check_interval", r->C}, {"move_budget", r->move_budget},
-        {"slice_moves", (int64_t)1 << 18}};
+        {"slice_moves", (int64_t)1 << 40}, {"slice_ms", 50}};
     for (const auto& o : opts)
         if ((st = wl_set_option(p->h, o.first, o.second))) return st;
     if ((st = wl::rt::prepare(p->h, r->u, r->flatness, nullptr))) return st;

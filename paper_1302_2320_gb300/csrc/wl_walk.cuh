@@ -199,6 +199,8 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
     const uint2 key = make_uint2((uint32_t)ell, A.seed);
     int64_t end = t + A.slice_moves;
     if (end > A.budget) end = A.budget;
+    // flatness check interval of this line: longer for lines with more bins
+    const int64_t C = A.C_per_bin > 0 && A.C_per_bin * nbins > A.C ? A.C_per_bin * nbins : A.C;
 
     int bc = k >> ks;
     int wb = window_base(bc, nbins);
@@ -216,7 +218,7 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
     bool needf = true;
 
     while (t < end && !stop) {
-        const int64_t next_check = (t / A.C + 1) * A.C;
+        const int64_t next_check = (t / C + 1) * C;
         const int64_t seg_end = next_check < end ? next_check : end;
         int left = (int)(seg_end - t);    // moves before the next check or the slice end
 
@@ -234,22 +236,25 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
             // accepted iff ln g(target) <= ln g(current before step m) + dmax, and
             // ln g(current before step m) = u + m F while the walker keeps its bin
             const int64_t base = mF + d0.dmax;
-            const uint32_t ab = kPack ? (a | (b << 16)) : a;
+            // U and D are lists of distinct sites, so a later proposal reuses
+            // list slot a_e (b_e) of an accepted exchange iff its i (j) is i_e (j_e)
             const uint32_t ij = kPack ? (i | (j << 16)) : i;
             if constexpr (TBL) {
-                // conflict filter: which lanes have a site among their neighbours
-                // (first half) or a list position (second half), hashed by the
-                // low bits; an accepted exchange looks up its own sites and slots
+                // conflict filter: for every site, the lanes that have it among
+                // their sites or their sites' neighbours (hashed by the low bits);
+                // an accepted exchange looks up its own two sites
                 const uint32_t tm = (uint32_t)A.tbl_mask, bit = 1u << m;
 #pragma unroll
                 for (int q = 0; q < zc; ++q) {
                     atomicOr(&tbl[ni[q] & tm], bit);
                     atomicOr(&tbl[nj[q] & tm], bit);
                 }
-                atomicOr(&tbl[tm + 1 + (a & tm)], bit);
-                atomicOr(&tbl[tm + 1 + ((ell + b) & tm)], bit);
+                atomicOr(&tbl[i & tm], bit);
+                atomicOr(&tbl[j & tm], bit);
                 __syncwarp(gmask);
             }
+            int rec_x = 0;        // the bin this lane's step left, and its visits (counted at the end)
+            uint32_t rec_c = 0u;
             // -- resolve.  One pass of the loop handles one accepted step (an
             // event): the walker's state is updated by selects, the later lanes
             // are evaluated again for the next event, and only the rare cases
@@ -283,19 +288,17 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
                 const int src = gbase + e;
                 const int dke = __shfl_sync(gmask, dk, src);
                 const int64_t ve = __shfl_sync(gmask, v, src);
-                const uint32_t abe = __shfl_sync(gmask, ab, src), ije = __shfl_sync(gmask, ij, src);
-                uint32_t be = 0, je = 0;
-                if constexpr (!kPack) {
-                    be = __shfl_sync(gmask, b, src);
-                    je = __shfl_sync(gmask, j, src);
-                }
+                const uint32_t ije = __shfl_sync(gmask, ij, src);
+                uint32_t je = 0;
+                if constexpr (!kPack) je = __shfl_sync(gmask, j, src);
                 const bool offe = (offb >> e) & 1u;  // walked off the window: ends the batch at e
                 // accepted step e: a new bin means steps e0 .. e-1 were rejections in the old one
                 const bool mv = (dke != 0) & !offe;
                 const int x = kw >> ks;
-                if (mv) {
-                    wl[x] = u + (int64_t)e * F;
-                    wd[x] += (uint32_t)(e - ent);
+                if (mv) wl[x] = u + (int64_t)e * F;
+                if (mv & (m == e)) {
+                    rec_x = x;
+                    rec_c = (uint32_t)(e - ent);
                 }
                 k = mv ? k + dke : k;
                 kw = mv ? kw + dke : kw;
@@ -312,19 +315,16 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
                 // batch short before it, one next to it gets its change of k shifted
                 const uint32_t ie = kPack ? (ije & 0xFFFFu) : ije;
                 if constexpr (kPack) je = ije >> 16;
-                const uint32_t xs = ab ^ abe;
+                const uint32_t xs = ij ^ ije;
                 bool conflict;
                 if constexpr (TBL) {
                     // lanes that may be affected (a superset); tested exactly below
                     const uint32_t tm = (uint32_t)A.tbl_mask;
-                    const uint32_t ae = kPack ? (abe & 0xFFFFu) : abe;
-                    if constexpr (kPack) be = abe >> 16;
-                    conflict = ((tbl[ie & tm] | tbl[je & tm] | tbl[tm + 1 + (ae & tm)] |
-                                 tbl[tm + 1 + ((ell + be) & tm)]) & live & ~done) != 0u;
+                    conflict = ((tbl[ie & tm] | tbl[je & tm]) & live & ~done) != 0u;
                 }
                 bool n0 = false, n1 = false, n2 = false, n3 = false, slot = false;
                 if constexpr (!TBL) {
-                    slot = kPack ? (((xs & 0xFFFFu) == 0u) | ((xs >> 16) == 0u)) : ((xs == 0u) | (b == be));
+                    slot = kPack ? (((xs & 0xFFFFu) == 0u) | ((xs >> 16) == 0u)) : ((xs == 0u) | (j == je));
 #pragma unroll
                     for (int q = 0; q < zc; ++q) {
                         n0 |= ni[q] == ie;
@@ -342,7 +342,7 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
                     conflict = (group_ballot<S>(gmask, gbase, slot | (n0 | n1) | (n2 | n3)) & live & ~done) != 0u;
                 if (conflict) {
                     if constexpr (TBL)
-                        slot = kPack ? (((xs & 0xFFFFu) == 0u) | ((xs >> 16) == 0u)) : ((xs == 0u) | (b == be));
+                        slot = kPack ? (((xs & 0xFFFFu) == 0u) | ((xs >> 16) == 0u)) : ((xs == 0u) | (j == je));
                     const unsigned sm = group_ballot<S>(gmask, gbase, slot) & live & ~done;
                     if (sm) {
                         lim_eff = __ffs(sm) - 1;             // > e
@@ -371,16 +371,18 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
             cur = u + (int64_t)c * F;
             pend = c - ent;
             if (c == 0) stop = 4;                  // step t always fits the window
+            // visits to the bins the walker left in this batch, one lane per bin left
+            __syncwarp(gmask);
+            if (rec_c) atomicAdd(wd + rec_x, rec_c);
             if constexpr (TBL) {
-                __syncwarp(gmask);
                 const uint32_t tm = (uint32_t)A.tbl_mask;
 #pragma unroll
                 for (int q = 0; q < zc; ++q) {
                     tbl[ni[q] & tm] = 0u;
                     tbl[nj[q] & tm] = 0u;
                 }
-                tbl[tm + 1 + (a & tm)] = 0u;
-                tbl[tm + 1 + ((ell + b) & tm)] = 0u;
+                tbl[i & tm] = 0u;
+                tbl[j & tm] = 0u;
             }
             // apply the accepted exchanges (distinct slots, distinct sites)
             if ((accm >> m) & 1u) {
@@ -437,7 +439,7 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
             __syncwarp(gmask);
             checks += 1;
             const bool flat = group_flat<S>(hist, nbins, m, gmask, A.flat_pm);
-            if (!flat && A.same_f_resets > 0 && (t - t_stage) / A.C <= A.same_f_resets) {
+            if (!flat && A.same_f_resets > 0 && (t - t_stage) / C <= A.same_f_resets) {
                 // extra reset at unchanged f within the first R checks of a
                 // stage (the remark after Eq. 4): histogram reset, ln g shifted
                 group_stage_step<S>(lng, hist, nbins, m, gmask);
@@ -538,7 +540,7 @@ __global__ void walk_kernel(const WalkArgs A)
     if constexpr (TBL) {
         // the conflict filter table starts empty and is left empty by every batch
         tbl = reinterpret_cast<uint32_t*>(slot);
-        const int words = 2 * (A.tbl_mask + 1);
+        const int words = A.tbl_mask + 1;
         for (int x = m; x < words; x += S) tbl[x] = 0u;
         __syncwarp(gmask);
         slot += (size_t)words * 4;

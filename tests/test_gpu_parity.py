@@ -460,3 +460,19 @@ def test_time_limited_slices_bit_exact(l12_ref):
     assert h.stats()["launches"] > 4                     # several slices
     for ell in range(73):
         assert_line_equal(h, ell, l12_ref[ell], "slice_ms=3")
+
+
+def test_check_interval_growing_with_bins_bit_exact():
+    """Option check_per_bin: a line of n bins checks flatness every
+    max(C, c n) moves.  The oracle walks each line with that interval; the
+    chains agree bit for bit."""
+    L, seed, u, C, cpb, budget = 12, 3, 1e-7, 1000, 40, 2_000_000
+    h = run_gpu("square", L, seed, u, C, budget, check_per_bin=cpb)
+
+    def one(ell):
+        nb = oracle.line_nbins(oracle.SQUARE, L, ell)
+        return oracle.run_line(oracle.SQUARE, L, ell, seed, u, max(C, cpb * nb), 800, budget, 0)
+    with ThreadPoolExecutor(THREADS) as ex:
+        ref = dict(zip(range(73), ex.map(one, range(73))))
+    for ell in range(73):
+        assert_line_equal(h, ell, ref[ell], "check_per_bin")
