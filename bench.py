@@ -451,7 +451,7 @@ def run_serve(args):
 
 def run_accuracy(args):
     """Accuracy of a whole surface against the exact transfer-matrix values
-    (tests/golden/square_L{L}_exact.txt, L = 8 or 12): seeds walked
+    (tests/golden/square_L{L}_exact.txt, L = 6, 8 or 12): seeds walked
     concurrently, production mode, to ln f_min; mean and max |d ln g_kl| over
     the inner bins and over the two ends of each line's spectrum (the lowest and
     highest k, where the paper also sees the largest deviations)."""
@@ -772,7 +772,7 @@ def main():
     ap.add_argument("--hbm-budget", type=int, default=32 << 30)
     ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--accuracy", action="store_true", help="accuracy against the exact surface")
-    ap.add_argument("--accuracy-L", type=int, default=12, choices=[8, 12])
+    ap.add_argument("--accuracy-L", type=int, default=12, choices=[6, 8, 12])
     ap.add_argument("--seeds", type=int, default=8)
     args = ap.parse_args()
     if args.accuracy:

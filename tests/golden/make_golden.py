@@ -2,8 +2,8 @@
 
     python tests/golden/make_golden.py [--threads N]
 
-square_L{8,12}_exact.txt: exact ln g_kl of the periodic 8x8 and 12x12 square
-Ising lattices (N_B = 2N) for l = 0..N/2, every k with g_kl > 0, from the
+square_L{6,8,12}_exact.txt: exact ln g_kl of the periodic 6x6, 8x8 and 12x12
+square Ising lattices (N_B = 2N) for l = 0..N/2, every k with g_kl > 0, from the
 oracle's site-by-site transfer matrix (the exact surface that Eq. 2 sums over;
 the paper cites transfer-matrix surfaces up to 12x12).  Columns: l, k, ln g_kl.
 cubic_L3_exact.txt: exact g_kl of the periodic 3x3x3 simple cubic lattice by
@@ -73,13 +73,15 @@ def write_square_gk(L):
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--threads", type=int, default=os.cpu_count() or 1)
-    ap.add_argument("--only", choices=["square", "square8", "cubic", "gk"], default=None)
+    ap.add_argument("--only", choices=["square", "square_small", "cubic", "gk"], default=None)
     a = ap.parse_args()
     if a.only in (None, "cubic"):
         write_cubic_l3()
-    if a.only == "square8":
+    if a.only == "square_small":
+        write_square_tm(6, a.threads)
         write_square_tm(8, a.threads)
     if a.only in (None, "square"):
+        write_square_tm(6, a.threads)
         write_square_tm(8, a.threads)
         write_square_tm(12, a.threads)
     if a.only in (None, "gk"):

@@ -332,22 +332,23 @@ def test_golden_l12_closed_forms():
     assert math.isclose(g[72][NB], math.log(2), abs_tol=1e-12)
 
 
-def test_golden_l8_closed_forms_and_tm():
-    """The stored 8x8 surface: row sums C(N, l), the closed forms of the small
-    lines and of l = N/2 (bands 2L at k = 2L, Neel at k = N_B), and equality
-    with the oracle's TM recomputed here (0.4 s)."""
-    L, N, NB = 8, 64, 128
+@pytest.mark.parametrize("L", [6, 8])
+def test_golden_small_surfaces_closed_forms_and_tm(L):
+    """The stored 6x6 and 8x8 surfaces: row sums C(N, l), the closed forms of
+    the small lines and of l = N/2 (bands 2L at k = 2L, Neel at k = N_B), and
+    equality with the oracle's TM recomputed here (under a second)."""
+    N, NB = L * L, 2 * L * L
     g = {}
-    for ell, k, lg in np.loadtxt(os.path.join(HERE, "golden", "square_L8_exact.txt")):
+    for ell, k, lg in np.loadtxt(os.path.join(HERE, "golden", f"square_L{L}_exact.txt")):
         g.setdefault(int(ell), {})[int(k)] = float(lg)
-    assert sorted(g) == list(range(33))
+    assert sorted(g) == list(range(N // 2 + 1))
     for ell, row in g.items():
         lse = np.logaddexp.reduce(np.array(list(row.values())))
         assert math.isclose(lse, math.log(math.comb(N, ell)), rel_tol=0, abs_tol=1e-11), ell
         assert max(row) == min(4 * ell, NB) and all(k % 2 == 0 for k in row)
     assert math.isclose(g[2][6], math.log(NB), abs_tol=1e-12)
-    assert math.isclose(g[32][2 * L], math.log(2 * L), abs_tol=1e-12)
-    assert math.isclose(g[32][NB], math.log(2), abs_tol=1e-12)
+    assert math.isclose(g[N // 2][2 * L], math.log(2 * L), abs_tol=1e-12)
+    assert math.isclose(g[N // 2][NB], math.log(2), abs_tol=1e-12)
     tm = oracle.tm_square(L, ell_max=N // 2)
     for ell, row in g.items():
         for k, lg in row.items():
