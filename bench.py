@@ -286,6 +286,8 @@ def run_converge(args):
                   same_f_resets=args.same_f_resets, form=args.form)
     if args.check_per_bin:
         h.set_option("check_per_bin", args.check_per_bin)
+    if args.move_budget:
+        h.set_option("move_budget", args.move_budget)
     if args.slice_ms > 0 and args.form == 0:
         # slices end by device time: no line waits for a slower one at a slice end
         h.set_option("slice_ms", args.slice_ms)
@@ -306,7 +308,7 @@ def run_converge(args):
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
-    rc = h.run(args.ln_f_min, FLATNESS, allow=(wl.WL_OK, wl.WL_ETIMEOUT))
+    rc = h.run(args.ln_f_min, FLATNESS, allow=(wl.WL_OK, wl.WL_ETIMEOUT, wl.WL_ENOTCONVERGED))
     sec = time.perf_counter() - t0
     st = h.stats()
     moves = [0] * (h.N // 2 + 1)
@@ -343,7 +345,8 @@ def run_converge(args):
             "ln_f_min": args.ln_f_min, "check_interval": args.check_interval,
             "check_per_bin": args.check_per_bin,
             "same_f_resets": args.same_f_resets, "n_gpus": world,
-            "status": "converged" if rc == wl.WL_OK else "time limit",
+            "status": {wl.WL_OK: "converged", wl.WL_ETIMEOUT: "time limit"}.get(rc, "move budget"),
+            "walk_ms": st["walk_ms"],
             "seconds": sec, "lines_converged": st["lines_converged"],
             "min_stage": st["min_stage"], "max_stage": st["max_stage"], "moves": st["moves"],
             "moves_per_s": st["moves"] / sec, "mapping": st["mapping"],
@@ -617,8 +620,15 @@ def run_ours(args):
     seed0 = rank_seed(rank)
     for w in range(max(args.warmup, 1)):
         step(seed0 + w)
-    mapping = h.stats()["mapping"]
-    h.set_option("mapping", mapping)            # autotuned choice, fixed for the timed steps
+    mapping = args.mapping
+    if mapping == 0:
+        # the lane-count tuner times one candidate per step: finish it, then fix its choice
+        extra = 0
+        while h.get_option("tuned_mapping") == 0 and extra < 3:
+            step(seed0 + 50 + extra)
+            extra += 1
+        mapping = h.get_option("tuned_mapping") or h.stats()["mapping"]
+    h.set_option("mapping", mapping)            # fixed for the timed steps
 
     clocks = ClockSampler(local)
     if rank == 0:
@@ -759,6 +769,7 @@ def main():
     ap.add_argument("--same-f-resets", type=int, default=0, help="extra same-f resets per stage")
     ap.add_argument("--slice-ms", type=int, default=100,
                     help="--converge: slices end after this much device time (0: by moves)")
+    ap.add_argument("--move-budget", type=int, default=0, help="--converge: per-line move cap (0: none)")
     ap.add_argument("--check-per-bin", type=int, default=0,
                     help="--converge: a line of n bins checks flatness every max(C, c n) moves")
     ap.add_argument("--cpu-converge", action="store_true",

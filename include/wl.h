@@ -124,6 +124,9 @@ size_t wl_required_bytes(wl_lattice lattice, int L);
  * Setting "seed", "deterministic", "check_interval", "check_per_bin", "same_f_resets" or the
  * line range after a run requires wl_reset().  Errors: WL_EINVAL (unknown key or bad value), WL_ESTATE. */
 wl_status wl_set_option(wl_handle h, const char* key, int64_t value);
+/* Read an option back; also the read-only keys "N", "NB", "z", "k_step",
+ * "lines", "bins", "device_bytes" and "tuned_mapping" (the lane count the tuner
+ * settled on for this lattice and mode, 0 while it is still timing candidates). */
 wl_status wl_get_option(wl_handle h, const char* key, int64_t* value);
 
 /* The walk of the method section, on every selected line: spin-exchange

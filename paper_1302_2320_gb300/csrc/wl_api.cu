@@ -889,6 +889,12 @@ wl_status wl_get_option(wl_handle h, const char* key, int64_t* v)
     else if (k == "slice_moves") *v = h->slice_moves;
     else if (k == "timeout_ms") *v = h->timeout_ms;
     else if (k == "slice_ms") *v = h->slice_ms;
+    else if (k == "tuned_mapping") {
+        // the lane count the tuner settled on for this lattice and mode (0: not yet)
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find({h->g.type, h->g.L, h->det});
+        *v = it != g_tune_cache.end() ? it->second.best : 0;
+    }
     else if (k == "hbm_budget") *v = h->hbm_budget;
     else if (k == "ell_min") *v = h->ell_min;
     else if (k == "same_f_resets") *v = h->same_f_resets;
