@@ -96,13 +96,17 @@ size_t wl_required_bytes(wl_lattice lattice, int L);
  *   "seed"           Philox key word 1 of every walker (default 1)
  *   "deterministic"  1: integer acceptance against the exp threshold table, the
  *                    chain bit-identical to the same walk taken one move at a
- *                    time (the CPU oracle's); 0: FP32 exp (default 1)
+ *                    time (the CPU oracle's); 0: FP32 (d <= -ln U / u) (default 1)
  *   "check_interval" C: flatness is tested whenever t is a multiple of C (default 1000)
  *   "check_per_bin"  c > 0: a line with n bins tests flatness every max(C, c*n)
  *                    moves instead, so lines with more bins get longer stages
  *                    and find their rarest states before ln f shrinks (default 0)
  *   "move_budget"    per-line cap on the move counter t (default 2^62)
- *   "mapping"        lanes per walker S in {1,2,4,8,16,32}; 0 = autotune (default 0)
+ *   "mapping"        lanes per walker S in {1,2,4,8,16,32}; 0 = tuned online: each
+ *                    of 32, 16, 8 walks one slice (timed with CUDA events), the
+ *                    fastest is kept, and they are timed again when the
+ *                    acceptance rate drifts by more than 0.15 (default 0).
+ *                    Every S walks the same chain.
  *   "form"           0: one persistent launch over all lines with a device
  *                    work queue; 1: one launch per line (default 0)
  *   "stream"         cudaStream_t (as an integer) for every launch (default: own stream)

@@ -17,20 +17,25 @@
 //     and the lanes are tested again only when an accepted step changes the
 //     bin or the proposals.
 // An accepted exchange of (i_e, j_e) changes a later proposal in two ways.  If
-// the proposal reuses list slot a_e or b_e its sites are no longer U[a], D[b]:
-// the batch is cut short before it.  If one of i_e, j_e neighbours its sites, its change of
-// k is off by 2 for every such neighbour (i_e turned down, j_e up): the later
-// lanes correct it in place and are tested again.  The exchanges accepted in a
-// batch touch distinct slots and distinct sites, so they are applied together
-// after the resolution.  Random numbers are keyed by t, so the committed chain
-// is the sequential chain, bit for bit, for every S.  Batches never cross a
+// the proposal reuses list slot a_e or b_e (equivalently: names site i_e or
+// j_e, the lists holding distinct sites) its sites are no longer U[a], D[b]:
+// the batch is cut short before it.  If one of i_e, j_e neighbours its sites,
+// its change of k is off by 2 for every such neighbour (i_e turned down, j_e
+// up): the later lanes correct it in place and are tested again.  The later
+// proposals an exchange may affect are found with 2z equality tests per lane,
+// or (TBL, the tail shape: one walker per block) with two loads from a
+// shared-memory table that lists, per site, the lanes having it among their
+// sites or their neighbours.  The exchanges accepted in a batch touch distinct
+// slots and distinct sites, so they are applied together after the resolution.
+// Random numbers are keyed by t, so the committed chain is the sequential
+// chain, bit for bit, for every S and both forms.  Batches never cross a
 // flatness check (t multiple of C) or the end of the slice.
 //
 // The current bin's ln g and its visits not yet counted live in registers; the
 // bins around it live in a shared-memory window (ln g, and the histogram counts
-// added since the window was loaded, by one lane when the walker leaves a
-// bin), written back when the walker re-centres it, at every check and at the
-// end.
+// added since the window was loaded: the visits to a bin the walker left are
+// added by the lane of the step that left it, at the end of the batch), written
+// back when the walker re-centres it, at every check and at the end.
 #pragma once
 
 #include "wl_device.cuh"
