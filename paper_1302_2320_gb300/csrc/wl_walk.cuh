@@ -305,11 +305,12 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
                     rec_x = x;
                     rec_c = (uint32_t)(e - ent);
                 }
-                k = mv ? k + dke : k;
-                kw = mv ? kw + dke : kw;
+                const int dkm = mv ? dke : 0;
+                k += dkm;
+                kw += dkm;
                 u = mv ? ve : u;
                 ent = mv ? e : ent;
-                accm |= offe ? 0u : (1u << e);
+                accm |= 1u << e;                     // withdrawn below if e walked off the window
                 done = (2u << e) - 1u;
                 // the later lanes against the new state
                 int wx = (kw + dk) >> ks;
@@ -340,6 +341,7 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
                 }
                 if (offe) {
                     if ((unsigned)((k + dke) >> ks) >= (unsigned)nbins) stop = 4;   // invariant broken
+                    accm &= ~(1u << e);
                     c = e;
                     break;
                 }
@@ -367,10 +369,7 @@ __device__ void walk_line(const WalkArgs& A, int li, int m, int gbase, unsigned 
                 v = ld - mF;
                 evb = group_ballot<S>(gmask, gbase, acc);
                 offb = group_ballot<S>(gmask, gbase, off);
-                if ((live & ~done) == 0u) {
-                    c = lim_eff;
-                    break;
-                }
+                // no step left: the next pass finds no event and ends the batch
             }
             bc = k >> ks;
             cur = u + (int64_t)c * F;
