@@ -538,15 +538,13 @@ int kernel_lattice(const wl_ctx* h)
     return h->g.type;
 }
 
-// 32 lanes per walker: on the 64x64 lattice a batch commits ~20 moves and this
+// 32 lanes per walker: on the 64x64 lattice a batch commits ~26 moves and this
 // mapping was fastest for every lattice measured.
 int pick_mapping_default(const wl_ctx*)
 {
     return 32;
 }
 
-// Persistent form: slices until every selected line converged or hit the
-// budget, or the run is stopped.
 // Persistent form: slices until every selected line converged or hit the
 // budget, or the run is stopped.
 //
